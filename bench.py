@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark: evidence cases/s of batched junction-tree inference on one GB300.
+
+One step = one full inference pass (evidence reduction, collect, distribute,
+log P(e) and posterior normalisation for every case) over one batch of the
+workload's evidence cases.  Default workload: the 60-variable network
+(cardinality 2..5, largest clique <= 1e5 entries) with 4096 cases and 10 %
+observed, synthetic and seeded (synth/).
+
+Reported on one JSON line (rank 0):
+  value       device-resident throughput (evidence already in HBM), cases/s
+  e2e         the same through jt_infer with host buffers (H2D of evidence and
+              D2H of results inside the timed region)
+  roofline    the dominant kernel's achieved algorithmic GB/s vs measured HBM peak
+  plain_gpu   the plain per-case FP64 GPU path on a sample of the same cases
+  cpu_baseline the FP64 oracle on the host cores on a bounded sample
+  accuracy    sampled outputs of the timed run against the FP64 oracle
+
+``--impl reference`` times the FP64 oracle (the reference arm for this build)
+on the host cores instead.  Under torchrun each rank processes its own batch
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "bn60": "bn60_card2-5_B4096_obs10pct",
+    "bn20": "bn20_binary_B100_obs20pct",
+    "bn110": "bn110_hub60_card2-8_B8192_obs15pct",
+    "bn420": "bn420_card2-4_Barena_obs5pct",
+    "bn1000": "bn1000_ternary_B4096_obs5-30pct",
+}
+DEFAULT_CASES = {"bn20": 100, "bn60": 4096, "bn110": 8192, "bn420": 1024, "bn1000": 4096}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_rate(net, ev, threads, budget_s):
+    """Oracle cases/s on up to len(ev) cases, stopping after ~budget_s."""
+    import oracle  # CPU baseline leg only
+    o = oracle.Oracle(net)
+    done, t0 = 0, time.perf_counter()
+    step = max(threads, 1) * 4
+    while done < ev.shape[0]:
+        o.infer(ev[done:done + step], threads=threads)
+        done = min(ev.shape[0], done + step)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_reference(args, name, net, ev, rank, world):
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    # one step = a bounded sample of the workload on all host cores
+    per_step = min(ev.shape[0], max(cores * 8, 64))
+    import oracle
+    o = oracle.Oracle(net)
+    for i in range(args.warmup):
+        o.infer(ev[:per_step], threads=cores)
+    times = []
+    for i in range(args.steps):
+        sl = ev[(i * per_step) % ev.shape[0]:][:per_step]
+        t0 = time.perf_counter()
+        o.infer(sl, threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = float(np.sum(times))
+    value = per_step * args.steps / total
+    line = {"metric": "evidence cases/sec at <=1e-5 posterior error", "value": value,
+            "unit": "cases/s", "impl": "reference", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS[name], "cases_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "cases/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} cases of the workload per step"},
+            "e2e": {"value": value, "unit": "cases/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bn60", choices=sorted(WORKLOADS))
+    ap.add_argument("--cases", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from synth import configs
+    name = args.workload
+    net = configs.network(name)
+    n_cases = args.cases or DEFAULT_CASES[name]
+    # every rank gets its own independent batch (weak scaling)
+    ev = configs.evidence(name, net, n_cases=n_cases,
+                          seed=configs.EVIDENCE_SEED[name] + 1000 * rank)
+
+    if args.impl == "reference":
+        return run_reference(args, name, net, ev, rank, world)
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    import paper_2212_04241_gb300.jt as J
+    plan = J.Plan(net)
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    d_ev = torch.from_numpy(ev).cuda()
+    d_lp = torch.empty(n_cases, dtype=torch.float64, device="cuda")
+    d_post = torch.empty((n_cases, plan.sum_card), dtype=torch.float64, device="cuda")
+    d_st = torch.empty(n_cases, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        plan.infer_device(d_ev, d_lp, d_post, d_st, stream=sptr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = plan.info()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = n_cases * world / (ms_per_step / 1e3)
+
+    # accuracy of the timed run's outputs on a seeded sample (oracle)
+    lp = d_lp.cpu().numpy()
+    post = d_post.cpu().numpy()
+    st = d_st.cpu().numpy()
+    accuracy = None
+    if rank == 0:
+        import oracle
+        idx = np.random.default_rng(0).choice(n_cases, size=min(64, n_cases), replace=False)
+        olp, opost, ost = oracle.Oracle(net).infer(ev[idx], threads=os.cpu_count() or 1)
+        ok = ost == 0
+        accuracy = {
+            "sample_cases": int(len(idx)),
+            "max_abs_posterior_err": float(np.max(np.abs(post[idx][ok] - opost[ok]))),
+            "max_rel_logpe_err": float(np.max(np.abs(lp[idx][ok] - olp[ok]) / np.maximum(1, np.abs(olp[ok])))),
+            "status_match": bool(np.array_equal(st[idx], ost)),
+        }
+        accuracy["pass"] = bool(accuracy["max_abs_posterior_err"] <= 1e-5 and
+                                accuracy["max_rel_logpe_err"] <= 1e-6 and accuracy["status_match"])
+
+    # per-kernel device time (instrumented pass, events around each layer launch)
+    prof = plan.profile(d_ev, d_lp, d_post, d_st, stream=sptr)
+    kinds = {"collect": prof["collect_ms"], "distribute": prof["distribute_ms"]}
+    dom = max(kinds, key=kinds.get)
+    # algorithmic bytes of one pass per kernel kind (per case):
+    #   collect:    psi written 4|C|, messages written 4|S| and read 4|S|
+    #   distribute: psi read 4|C|, ratios written 4|S| and read 4|S|
+    per_case = 4.0 * info["sum_clique_entries"] + 8.0 * info["sum_sep_entries"]
+    bytes_dom = per_case * n_cases
+    achieved = bytes_dom / (kinds[dom] / 1e3) / 1e9
+    peak, peak_src = _peaks()
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "launches": prof[f"{dom}_launches"],
+                "kernel_ms_per_pass": kinds[dom], "other_kernel_ms_per_pass": kinds["collect" if dom == "distribute" else "distribute"],
+                "whole_pass_algorithmic_GBps": info["algorithmic_bytes_per_case"] * n_cases / (prof["total_ms"] / 1e3) / 1e9}
+
+    # end to end through jt_infer with host buffers
+    e2e = None
+    if rank == 0:
+        import torch as _t
+        ev_pinned = _t.from_numpy(ev).pin_memory().numpy()
+        plan.infer(ev_pinned)
+        reps = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            plan.infer(ev_pinned)
+        dt = (time.perf_counter() - t0) / reps
+        e2e = {"value": n_cases / dt, "unit": "cases/s", "h2d_bytes_per_step": int(ev.nbytes),
+               "d2h_bytes_per_step": int(n_cases * (8 + 8 * plan.sum_card + 4)), "ms_per_step": dt * 1e3}
+
+    plain = None
+    if rank == 0 and not args.no_plain:
+        m = min(n_cases, 64 if name in ("bn20", "bn60", "bn1000") else 8)
+        plan.infer_plain(ev[:2])
+        t0 = time.perf_counter()
+        plan.infer_plain(ev[:m])
+        dt = time.perf_counter() - t0
+        plain = {"value": m / dt, "unit": "cases/s", "sample": f"first {m} cases", "dtype": "f64",
+                 "batched_over_plain": value / world / (m / dt)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, done, dt = _oracle_rate(net, ev, cores, 15.0)
+        cpu = {"value": rate, "unit": "cases/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} cases of the workload in {dt:.1f} s"}
+
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    launches = info["kernels_per_chunk"] * ((n_cases + info["chunk_cases"] - 1) // max(1, info["chunk_cases"]))
+    line = {
+        "metric": "evidence cases/sec at <=1e-5 posterior error (batched FP32 path)",
+        "value": value, "unit": "cases/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[name], "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
+                   "chunk_cases": info["chunk_cases"], "levels": info["n_levels"],
+                   "sum_clique_entries": info["sum_clique_entries"],
+                   "l2": "inputs larger than L2 (psi arena %.2f GB per step)" % (4.0 * info["sum_clique_entries"] * n_cases / 1e9),
+                   "parallelism": f"cases sharded, {world} rank(s)"},
+        "gpu_launches": int(launches * args.steps),
+        "roofline": roofline, "clocks": clock_info, "e2e": e2e, "plain_gpu": plain,
+        "cpu_baseline": cpu, "accuracy": accuracy,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,254 @@
+/*
+ * jt.h -- C ABI of the GB300 junction-tree exact-inference library.
+ *
+ * The library answers the exact-inference query of a Bayesian network (BN):
+ * given evidence e on some variables, P(e) and the posterior marginal
+ * P(X_v | e) of every unobserved variable (Section 1 of "POSTER: Fast
+ * Parallel Exact Inference on Bayesian Networks", the problem statement).
+ * It follows the junction-tree route described there: the BN is compiled
+ * once into a tree of cliques joined by separators, each with a potential
+ * table (Section 1), and every query passes messages along the tree with
+ * the three table operations of Section 2 -- marginalisation, extension and
+ * reduction (evidence) -- plus Hugin separator division.  Cliques are
+ * grouped into tree layers (Section 2, BFS traversal); one GPU launch
+ * processes a whole layer for a whole batch of evidence cases, which is the
+ * GPU counterpart of the paper's per-layer flattening of all table entries
+ * into one parallel task (Section 2, hybrid parallelism).
+ *
+ * Conventions shared by every call:
+ *   - Variables are numbered 0..n-1.  card[v] >= 2 is the number of states.
+ *   - Parents are given in CSR form: the parents of v are
+ *     parents[parent_ptr[v] .. parent_ptr[v+1]-1]; the graph must be acyclic.
+ *   - cpt is all conditional probability tables concatenated in variable
+ *     order.  The table of v has one row per joint configuration of its
+ *     parents (mixed radix, the first listed parent varies slowest) and
+ *     card[v] columns (the child's state varies fastest).  Entries must be
+ *     >= 0 and every row must sum to 1 within 1e-6.
+ *   - Evidence is int32 [n_cases][n]: the observed state of v, or -1.
+ *   - Outputs: log_pe float64 [n_cases] (natural log of P(e));
+ *     posteriors float64 [n_cases][sum(card)], the states of v at offsets
+ *     sum(card[0..v-1]) ...; an observed variable gets a point mass;
+ *     case_status int32 [n_cases] (JT_CASE_*).
+ *   - Every call returns a jt_status and never aborts.  The caller owns all
+ *     buffers it passes; inputs are read during the call only.
+ *   - Accuracy of the FP32 batched path against exact FP64 arithmetic:
+ *     max abs posterior error <= 1e-5 and |d log P(e)| <= 1e-6*max(1,|log P(e)|)
+ *     on the workloads this library is tested on.
+ */
+#ifndef JT_H
+#define JT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define JT_API __attribute__((visibility("default")))
+#else
+#define JT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jt_plan jt_plan;     /* opaque; owns all device memory of a compiled network */
+typedef struct jt_server jt_server; /* opaque; continuous-batching request loop */
+
+typedef enum {
+  JT_OK = 0,
+  JT_EINVAL = 1,    /* bad argument, CPT or evidence shape */
+  JT_ECYCLE = 2,    /* the parent graph has a directed cycle */
+  JT_ETOOBIG = 3,   /* a clique table exceeds max_clique_entries */
+  JT_ENOMEM = 4,    /* device or host allocation failed / arena too small */
+  JT_ECUDA = 5,     /* a CUDA call failed (see jt_last_error) */
+  JT_ETIMEOUT = 6,  /* a bounded device wait expired */
+  JT_EBUSY = 7,     /* serving: result not ready yet */
+  JT_ENOTFOUND = 8  /* serving: unknown plan id or ticket */
+} jt_status;
+
+enum {
+  JT_CASE_OK = 0,
+  JT_CASE_ZERO_EVIDENCE = 1, /* P(e) = 0: log_pe = -inf, posteriors NaN */
+  JT_CASE_BAD_EVIDENCE = 2   /* a state outside [-1, card-1]: outputs NaN */
+};
+
+enum {
+  JT_ROOT_LARGEST = 0,   /* root = largest clique table (ties: lowest id) */
+  JT_ROOT_MIN_HEIGHT = 1 /* root = clique of least eccentricity, i.e. fewest
+                            layers (Section 2, root selection strategy);
+                            ties: larger table, then lowest id */
+};
+
+typedef struct {
+  int32_t root_rule;          /* JT_ROOT_* (default JT_ROOT_MIN_HEIGHT) */
+  int32_t host_only;          /* 1: compile on the host only, allocate no
+                                 device memory (inference calls then return
+                                 JT_EINVAL); used to inspect a plan */
+  int32_t cases_per_thread;   /* 1, 2 or 4: each GPU thread carries this many
+                                 evidence cases, a case tile is 32x that;
+                                 0 = automatic (4) */
+  int32_t rows_per_cta;       /* table rows (entries) per thread block of a
+                                 layer launch; 0 = automatic (per plan) */
+  int64_t max_clique_entries; /* JT_ETOOBIG above this; 0 = 2^31 - 1 */
+  int64_t arena_bytes;        /* device bytes for per-batch tables; the
+                                 batch is processed in chunks that fit;
+                                 0 = automatic (min(96 GiB, 60% of free)) */
+  int32_t use_graphs;         /* 1 (default): replay the layer launches of a
+                                 batch chunk as one captured CUDA graph */
+  int32_t reserved[7];
+} jt_compile_opts;
+
+typedef struct {
+  int32_t n_vars;
+  int32_t n_cliques;
+  int32_t n_levels;             /* tree height + 1 */
+  int32_t root;
+  int64_t sum_clique_entries;   /* sum over cliques of |C| */
+  int64_t max_clique_entries;
+  int64_t sum_sep_entries;      /* sum over separators of |S| */
+  int64_t sum_card;             /* length of one posterior row */
+  int32_t tile_cases;           /* evidence cases per tile (32 * cases_per_thread) */
+  int32_t chunk_cases;          /* cases per arena chunk (multiple of tile_cases) */
+  int64_t arena_bytes;          /* bytes of the per-batch arena actually used */
+  int64_t static_device_bytes;  /* base tables, index maps, work lists */
+  int64_t collect_items;        /* thread blocks per tile, all collect layers */
+  int64_t distribute_items;     /* thread blocks per tile, all distribute layers */
+  double algorithmic_bytes_per_case; /* 8*sum|C| + 16*sum|S| + 4n + 8*sum(card) + 8 */
+  int32_t kernels_per_chunk;    /* kernel launches of one batch chunk */
+  int32_t pad;
+} jt_plan_info_t;
+
+/* Fill opts with the defaults listed above. */
+JT_API void jt_default_opts(jt_compile_opts *opts);
+
+/*
+ * Compile a network into a plan (host side; Section 1's secondary structure
+ * and Section 2's layering): moralise, triangulate by min-fill elimination
+ * (ties to the lowest variable id), keep the maximal elimination cliques,
+ * join them by a maximum-weight spanning tree on the number of shared
+ * variables, choose the root (opts->root_rule), group cliques into BFS
+ * layers, order every clique's variables so that its separator towards the
+ * parent is the outermost (slowest) block of its table, precompute the
+ * index maps of every table operation, upload everything to the current
+ * CUDA device.  All arrays are host pointers; they are copied.  opts may be
+ * NULL for the defaults.  On success *out owns the plan; free it with
+ * jt_plan_free.  Errors: JT_EINVAL (shapes, CPT rows), JT_ECYCLE,
+ * JT_ETOOBIG, JT_ENOMEM, JT_ECUDA.
+ */
+JT_API jt_status jt_compile(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
+                     const int32_t *parents, const double *cpt, const jt_compile_opts *opts,
+                     jt_plan **out);
+
+/*
+ * Batched FP32 inference with HOST buffers (Section 1's query for every case
+ * of the batch).  Copies the evidence to the device, runs the collect and
+ * distribute layers (FP32 tables, power-of-two rescaling, FP64 log P(e) and
+ * posterior normalisation), and copies the results back; the call returns
+ * after the results are in the caller's buffers.  cuda_stream is a
+ * cudaStream_t or NULL for the plan's own stream.  Any n_cases >= 0.
+ */
+JT_API jt_status jt_infer(jt_plan *plan, int32_t n_cases, const int32_t *evidence, double *log_pe,
+                   double *posteriors, int32_t *case_status, void *cuda_stream);
+
+/*
+ * Same as jt_infer with DEVICE buffers (all four pointers on the plan's
+ * device).  Work is enqueued on cuda_stream (NULL = the plan's stream) and
+ * the call returns without synchronising; the outputs are valid once the
+ * stream has reached that point.  Evidence states outside [-1, card-1] give
+ * JT_CASE_BAD_EVIDENCE for that case only.
+ */
+JT_API jt_status jt_infer_device(jt_plan *plan, int32_t n_cases, const int32_t *d_evidence,
+                          double *d_log_pe, double *d_posteriors, int32_t *d_case_status,
+                          void *cuda_stream);
+
+/*
+ * The plain per-case FP64 GPU path (measurement comparator, element-wise
+ * style of the prior GPU approach the paper compares against, Section 1 and
+ * Section 3 "Elem."): the same plan, FP64 tables, one case at a time, one
+ * kernel launch per table operation per tree edge, one thread per table
+ * entry, mixed-radix indices by division, FP64 atomicAdd marginalisation,
+ * no fusion, no graphs, no rescaling.  HOST buffers; synchronous.
+ */
+JT_API jt_status jt_infer_plain(jt_plan *plan, int32_t n_cases, const int32_t *evidence,
+                         double *log_pe, double *posteriors, int32_t *case_status,
+                         void *cuda_stream);
+
+/*
+ * Instrumented run of jt_infer_device (device buffers, same arguments) for
+ * measurement: the layer launches are issued one by one (no graph) with a
+ * CUDA event around each, on cuda_stream, and the call synchronises.
+ * out[0] total ms of the collect launches, out[1] total ms of the
+ * distribute launches, out[2] ms of the evidence and finalize launches,
+ * out[3] number of collect launches, out[4] number of distribute launches,
+ * out[5] the whole run's ms.  The results are written like jt_infer_device.
+ */
+JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evidence,
+                            double *d_log_pe, double *d_posteriors, int32_t *d_case_status,
+                            void *cuda_stream, double *out);
+
+/* Sizes and layout of a compiled plan. */
+JT_API jt_status jt_plan_info(const jt_plan *plan, jt_plan_info_t *out);
+
+/*
+ * Structure of clique c (for inspection and tests): its variables in table
+ * layout order (upward separator first), its parent clique (-1 for the
+ * root) and its depth.  vars must hold 64 entries; *n_vars receives the
+ * count.
+ */
+JT_API jt_status jt_plan_clique(const jt_plan *plan, int32_t c, int32_t *n_vars, int32_t *vars,
+                         int32_t *parent, int32_t *depth);
+
+/* Release a plan and all of its device memory (NULL is ignored). */
+JT_API void jt_plan_free(jt_plan *plan);
+
+/* Static text for a status code. */
+JT_API const char *jt_status_string(jt_status status);
+
+/* Text of the last error on the calling thread ("" if none). */
+JT_API const char *jt_last_error(void);
+
+/*
+ * Serving: a continuous-batching request loop (one host thread) over
+ * resident plans.  Requests are single evidence cases; the loop coalesces
+ * pending requests of the same plan into batches, admits a batch when its
+ * arena bytes fit the server's budget (arena_bytes; 0 = 16 GiB), keeps up to
+ * max_inflight batches in flight on separate CUDA streams so that batches
+ * of different plans overlap on the device, and hands results back by
+ * ticket.  A request's result does not depend on which other requests
+ * share its batch (fixed per-case reduction order).
+ */
+JT_API jt_status jt_server_create(int64_t arena_bytes, int32_t max_batch, int32_t max_inflight,
+                           jt_server **out);
+/* Register a plan (not copied; it must outlive the server). */
+JT_API jt_status jt_server_add_plan(jt_server *srv, jt_plan *plan, int32_t *plan_id);
+/*
+ * Queue one case.  evidence: int32 [n_vars of the plan]; query_vars: the
+ * variables whose posteriors the caller wants (n_query entries, or NULL and
+ * 0 for all).  Returns a ticket.
+ */
+JT_API jt_status jt_submit(jt_server *srv, int32_t plan_id, const int32_t *evidence,
+                    const int32_t *query_vars, int32_t n_query, uint64_t *ticket);
+/*
+ * Fetch a result: JT_EBUSY while pending.  post receives the posteriors of
+ * the queried variables concatenated in query order (all variables, in
+ * layout of the plan's sum(card) row, when the query was NULL).  On JT_OK
+ * the ticket is released.
+ */
+JT_API jt_status jt_poll(jt_server *srv, uint64_t ticket, double *log_pe, double *post,
+                  int32_t *case_status);
+/* Block until every submitted request has completed. */
+JT_API jt_status jt_server_drain(jt_server *srv);
+/*
+ * Counters: out[0] completed requests, out[1] batches launched, out[2]
+ * largest batch, out[3] peak arena bytes in use, out[4] p50 latency (ns),
+ * out[5] p99 latency (ns), out[6] requests pending.  Latency is submit ->
+ * result ready on the host.
+ */
+JT_API jt_status jt_server_stats(jt_server *srv, int64_t *out);
+JT_API void jt_server_destroy(jt_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JT_H */

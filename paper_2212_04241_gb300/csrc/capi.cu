@@ -1,0 +1,675 @@
+// C ABI: plan lifetime, table arena, layer scheduling (CUDA graphs), the
+// batched and plain inference drivers.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "kernels.cuh"
+#include "runtime.h"
+
+namespace jt {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+#define JT_CUDA_TRY(expr)                                                     \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess) {                                                  \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));          \
+      return JT_ECUDA;                                                        \
+    }                                                                         \
+  } while (0)
+
+static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// arena
+// ---------------------------------------------------------------------------
+ArenaLayout arena_layout(const Plan &P) {
+  ArenaLayout L{};
+  const size_t W = (size_t)P.tile;
+  L.psi = align_up(sizeof(float) * W * (size_t)P.sum_cl);
+  L.sep = align_up(sizeof(float) * W * (size_t)P.sep_rows);
+  L.post = align_up(sizeof(float) * W * (size_t)P.sum_card);
+  L.partial = align_up(sizeof(float) * W * (size_t)std::max<int64_t>(1, P.n_partials));
+  L.maxbits = align_up(sizeof(uint32_t) * W * P.cl.size());
+  L.counters = align_up(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, P.n_groups));
+  L.ev = align_up(sizeof(int32_t) * W * (size_t)P.n);
+  L.bad = align_up(sizeof(int32_t) * W);
+  L.per_tile = L.psi + 2 * L.sep + L.post + L.partial + L.maxbits + L.counters + L.ev + L.bad;
+  return L;
+}
+
+void arena_free(Arena &a) {
+  for (auto &kv : a.graphs) cudaGraphExecDestroy(kv.second);
+  a.graphs.clear();
+  if (a.mem && a.owns) cudaFree(a.mem);
+  a.mem = nullptr;
+  a.bytes = 0;
+  a.tiles = 0;
+}
+
+static void arena_bind(const Plan &P, Arena &a, char *mem, int tiles) {
+  const ArenaLayout L = arena_layout(P);
+  size_t off = 0;
+  auto take = [&](size_t per_tile) {
+    char *p = mem + off;
+    off += per_tile * (size_t)tiles;
+    return p;
+  };
+  a.da.psi = reinterpret_cast<float *>(take(L.psi));
+  a.da.phistar = reinterpret_cast<float *>(take(L.sep));
+  a.da.rho = reinterpret_cast<float *>(take(L.sep));
+  a.da.post = reinterpret_cast<float *>(take(L.post));
+  a.da.partial = reinterpret_cast<float *>(take(L.partial));
+  a.da.maxbits = reinterpret_cast<uint32_t *>(take(L.maxbits));
+  a.da.counters = reinterpret_cast<uint32_t *>(take(L.counters));
+  a.da.ev = reinterpret_cast<int32_t *>(take(L.ev));
+  a.da.bad = reinterpret_cast<int32_t *>(take(L.bad));
+  a.da.tiles = tiles;
+  a.mem = mem;
+  a.bytes = off;
+  a.tiles = tiles;
+}
+
+jt_status arena_alloc(const Plan &P, Arena &a, int tiles) {
+  arena_free(a);
+  const ArenaLayout L = arena_layout(P);
+  void *mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, L.per_tile * (size_t)tiles);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("arena cudaMalloc: ") + cudaGetErrorString(e));
+    return JT_ENOMEM;
+  }
+  a.owns = true;
+  arena_bind(P, a, static_cast<char *>(mem), tiles);
+  // counters start at zero; every combining block resets its own counter
+  JT_CUDA_TRY(cudaMemset(a.da.counters, 0, L.counters * (size_t)tiles));
+  return JT_OK;
+}
+
+jt_status arena_wrap(const Plan &P, Arena &a, void *mem, size_t bytes, int tiles) {
+  arena_free(a);
+  const ArenaLayout L = arena_layout(P);
+  if (L.per_tile * (size_t)tiles > bytes) {
+    set_error("arena buffer too small");
+    return JT_ENOMEM;
+  }
+  a.owns = false;
+  arena_bind(P, a, static_cast<char *>(mem), tiles);
+  return JT_OK;
+}
+
+// Enqueue the layer launches of one chunk: collect deepest layer first,
+// then distribute from the root down (Section 2's BFS layers).
+static void enqueue_layers(const jt_plan *pl, const DevArena &A, cudaStream_t s) {
+  const Plan &P = pl->P;
+  cudaMemsetAsync(A.maxbits, 0, arena_layout(P).maxbits * (size_t)A.tiles, s);
+  for (int L = P.height; L >= 0; --L) {
+    const Level &lv = P.levels[L];
+    launch_collect(P.cpt_per_thread, pl->dp, A, lv.c_item_begin, lv.c_item_end - lv.c_item_begin,
+                   lv.c_max_maps, s);
+  }
+  for (int L = 0; L <= P.height; ++L) {
+    const Level &lv = P.levels[L];
+    launch_distribute(P.cpt_per_thread, pl->dp, A, lv.d_item_begin, lv.d_item_end - lv.d_item_begin, s);
+  }
+}
+
+static jt_status graph_for(jt_plan *pl, Arena &a, int tiles, cudaGraphExec_t *out) {
+  auto it = a.graphs.find(tiles);
+  if (it != a.graphs.end()) { *out = it->second; return JT_OK; }
+  DevArena A = a.da;
+  A.tiles = tiles;
+  cudaGraph_t g = nullptr;
+  JT_CUDA_TRY(cudaStreamBeginCapture(pl->capture_stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_layers(pl, A, pl->capture_stream);
+  cudaError_t e = cudaStreamEndCapture(pl->capture_stream, &g);
+  if (e != cudaSuccess) {
+    set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+    return JT_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return JT_ECUDA;
+  }
+  a.graphs[tiles] = ex;
+  *out = ex;
+  return JT_OK;
+}
+
+jt_status run_chunk(jt_plan *pl, Arena &a, const int32_t *d_ev, int32_t nc, double *d_lp,
+                    double *d_post, int32_t *d_st, cudaStream_t s) {
+  const Plan &P = pl->P;
+  const int W = P.tile;
+  const int tiles = (nc + W - 1) / W;
+  if (tiles <= 0) return JT_OK;
+  if (tiles > a.tiles) { set_error("chunk larger than arena"); return JT_EINVAL; }
+  DevArena A = a.da;
+  A.tiles = tiles;
+  JT_CUDA_TRY(cudaMemsetAsync(A.bad, 0, arena_layout(P).bad * (size_t)tiles, s));
+  launch_evidence(P.cpt_per_thread, d_ev, nc, pl->dp, A, s);
+  if (P.opts.use_graphs) {
+    cudaGraphExec_t ex;
+    jt_status st = graph_for(pl, a, tiles, &ex);
+    if (st != JT_OK) return st;
+    JT_CUDA_TRY(cudaGraphLaunch(ex, s));
+  } else {
+    enqueue_layers(pl, A, s);
+  }
+  launch_finalize(P.cpt_per_thread, pl->dp, A, nc, P.dcl[P.root].sep_row, d_lp, d_post, d_st, s);
+  JT_CUDA_TRY(cudaGetLastError());
+  return JT_OK;
+}
+
+int budget_tiles(const jt_plan *pl, int64_t budget_bytes) {
+  const ArenaLayout L = arena_layout(pl->P);
+  if (budget_bytes <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    budget_bytes = std::min<int64_t>(96LL << 30, (int64_t)(0.6 * (double)fr));
+  }
+  return (int)std::min<int64_t>(budget_bytes / (int64_t)L.per_tile, kMaxTilesPerChunk);
+}
+
+// Make the plan's default arena hold at least min(need, budget) tiles.
+static jt_status ensure_default_arena(jt_plan *pl, int need_tiles) {
+  int want = need_tiles;
+  if (pl->budget_tiles_cache <= 0) pl->budget_tiles_cache = budget_tiles(pl, pl->P.opts.arena_bytes);
+  want = std::min(want, pl->budget_tiles_cache);
+  if (want <= 0) {
+    set_error("arena budget is smaller than one case tile");
+    return JT_ENOMEM;
+  }
+  if (pl->arena.tiles >= want) return JT_OK;
+  return arena_alloc(pl->P, pl->arena, want);
+}
+
+}  // namespace jt
+
+using namespace jt;
+
+// ---------------------------------------------------------------------------
+// plan lifetime
+// ---------------------------------------------------------------------------
+extern "C" void jt_default_opts(jt_compile_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->root_rule = JT_ROOT_MIN_HEIGHT;
+  o->host_only = 0;
+  o->cases_per_thread = 0;
+  o->rows_per_cta = 0;
+  o->max_clique_entries = 0;
+  o->arena_bytes = 0;
+  o->use_graphs = 1;
+}
+
+template <class T>
+static size_t put(std::vector<char> &blob, const std::vector<T> &v) {
+  size_t off = align_up(blob.size());
+  blob.resize(off + align_up(sizeof(T) * std::max<size_t>(1, v.size())), 0);
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), sizeof(T) * v.size());
+  return off;
+}
+
+static jt_status upload_plan(jt_plan *pl) {
+  Plan &P = pl->P;
+  std::vector<char> blob;
+  std::vector<int32_t> card32(P.card.begin(), P.card.end());
+  const size_t o_cl = put(blob, P.dcl), o_map = put(blob, P.dmap), o_task = put(blob, P.dtask);
+  const size_t o_ci = put(blob, P.citems), o_di = put(blob, P.ditems), o_ip = put(blob, P.ipool);
+  const size_t o_b32 = put(blob, P.base32), o_card = put(blob, card32), o_po = put(blob, P.post_off);
+  JT_CUDA_TRY(cudaMalloc(&pl->d_static, blob.size()));
+  pl->static_bytes = blob.size();
+  JT_CUDA_TRY(cudaMemcpy(pl->d_static, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  char *b = static_cast<char *>(pl->d_static);
+  DevPlan &D = pl->dp;
+  D.cl = reinterpret_cast<const DClique *>(b + o_cl);
+  D.maps = reinterpret_cast<const DMap *>(b + o_map);
+  D.tasks = reinterpret_cast<const DTask *>(b + o_task);
+  D.citems = reinterpret_cast<const DItem *>(b + o_ci);
+  D.ditems = reinterpret_cast<const DItem *>(b + o_di);
+  D.ipool = reinterpret_cast<const int32_t *>(b + o_ip);
+  D.base32 = reinterpret_cast<const float *>(b + o_b32);
+  D.card = reinterpret_cast<const int32_t *>(b + o_card);
+  D.post_off = reinterpret_cast<const int64_t *>(b + o_po);
+  D.n_vars = P.n;
+  D.n_cliques = (int32_t)P.cl.size();
+  D.root = P.root;
+  D.base_exp_sum = P.base_exp_sum;
+  D.psi_rows = P.sum_cl;
+  D.sep_rows = P.sep_rows;
+  D.post_rows = P.sum_card;
+  D.n_partials = std::max<int64_t>(1, P.n_partials);
+  D.n_groups = std::max<int64_t>(1, P.n_groups);
+  int max_maps = 0;
+  for (const Level &lv : P.levels) max_maps = std::max(max_maps, lv.c_max_maps);
+  const size_t smem = collect_smem_bytes(P.cpt_per_thread, max_maps);
+  if (smem > 227 * 1024) {
+    set_error("a clique has too many child messages and evidence variables for one thread block");
+    return JT_ETOOBIG;
+  }
+  JT_CUDA_TRY(configure_collect_smem(P.cpt_per_thread, smem));
+  return JT_OK;
+}
+
+extern "C" jt_status jt_compile(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
+                                const int32_t *parents, const double *cpt, const jt_compile_opts *opts,
+                                jt_plan **out) {
+  if (!out) { set_error("out is NULL"); return JT_EINVAL; }
+  *out = nullptr;
+  jt_compile_opts o;
+  if (opts) o = *opts; else jt_default_opts(&o);
+  jt_plan *pl = new (std::nothrow) jt_plan();
+  if (!pl) return JT_ENOMEM;
+  std::string err;
+  jt_status st;
+  try {
+    st = build_plan(n_vars, card, parent_ptr, parents, cpt, o, pl->P, err);
+  } catch (const std::bad_alloc &) {
+    st = JT_ENOMEM;
+    err = "host allocation failed while compiling";
+  }
+  if (st != JT_OK) {
+    set_error(err);
+    delete pl;
+    return st;
+  }
+  pl->host_only = o.host_only != 0;
+  if (!pl->host_only) {
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("no CUDA device");
+      delete pl;
+      return JT_ECUDA;
+    }
+    if (cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pl->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("stream creation failed");
+      jt_plan_free(pl);
+      return JT_ECUDA;
+    }
+    st = upload_plan(pl);
+    if (st != JT_OK) {
+      jt_plan_free(pl);
+      return st;
+    }
+  }
+  *out = pl;
+  return JT_OK;
+}
+
+static void free_io(jt_plan *pl) {
+  if (pl->d_io) cudaFree(pl->d_io);
+  if (pl->h_io) cudaFreeHost(pl->h_io);
+  pl->d_io = pl->h_io = nullptr;
+  pl->io_cases = 0;
+}
+
+extern "C" void jt_plan_free(jt_plan *pl) {
+  if (!pl) return;
+  if (!pl->host_only) {
+    arena_free(pl->arena);
+    free_io(pl);
+    if (pl->d_plain) cudaFree(pl->d_plain);
+    if (pl->d_static) cudaFree(pl->d_static);
+    if (pl->stream) cudaStreamDestroy(pl->stream);
+    if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
+  }
+  delete pl;
+}
+
+extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
+  if (!pl || !o) { set_error("null argument"); return JT_EINVAL; }
+  const Plan &P = pl->P;
+  std::memset(o, 0, sizeof(*o));
+  o->n_vars = P.n;
+  o->n_cliques = (int32_t)P.cl.size();
+  o->n_levels = P.height + 1;
+  o->root = P.root;
+  o->sum_clique_entries = P.sum_cl;
+  o->max_clique_entries = P.max_cl;
+  o->sum_sep_entries = P.sum_sep;
+  o->sum_card = P.sum_card;
+  o->tile_cases = P.tile;
+  o->chunk_cases = pl->arena.tiles * P.tile;
+  o->arena_bytes = (int64_t)pl->arena.bytes;
+  o->static_device_bytes = (int64_t)pl->static_bytes;
+  o->collect_items = (int64_t)P.citems.size();
+  o->distribute_items = (int64_t)P.ditems.size();
+  o->algorithmic_bytes_per_case = 8.0 * (double)P.sum_cl + 16.0 * (double)P.sum_sep + 4.0 * P.n +
+                                  8.0 * (double)P.sum_card + 8.0;
+  int k = 2;  // evidence + finalize
+  for (const Level &lv : P.levels) {
+    k += lv.c_item_end > lv.c_item_begin;
+    k += lv.d_item_end > lv.d_item_begin;
+  }
+  o->kernels_per_chunk = k;
+  return JT_OK;
+}
+
+extern "C" jt_status jt_plan_clique(const jt_plan *pl, int32_t c, int32_t *n_vars, int32_t *vars,
+                                    int32_t *parent, int32_t *depth) {
+  if (!pl || c < 0 || c >= (int32_t)pl->P.cl.size()) { set_error("bad clique id"); return JT_EINVAL; }
+  const HostClique &C = pl->P.cl[c];
+  if (n_vars) *n_vars = (int32_t)C.vars.size();
+  if (vars) for (size_t i = 0; i < C.vars.size() && i < 64; ++i) vars[i] = C.vars[i];
+  if (parent) *parent = C.parent;
+  if (depth) *depth = C.depth;
+  return JT_OK;
+}
+
+extern "C" const char *jt_status_string(jt_status s) {
+  switch (s) {
+    case JT_OK: return "ok";
+    case JT_EINVAL: return "invalid argument";
+    case JT_ECYCLE: return "parent graph has a cycle";
+    case JT_ETOOBIG: return "clique table too large";
+    case JT_ENOMEM: return "out of memory";
+    case JT_ECUDA: return "CUDA error";
+    case JT_ETIMEOUT: return "device wait timed out";
+    case JT_EBUSY: return "not ready";
+    case JT_ENOTFOUND: return "not found";
+  }
+  return "unknown status";
+}
+
+extern "C" const char *jt_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// batched inference
+// ---------------------------------------------------------------------------
+static cudaStream_t pick_stream(jt_plan *pl, void *s) {
+  return s ? static_cast<cudaStream_t>(s) : pl->stream;
+}
+
+extern "C" jt_status jt_infer_device(jt_plan *pl, int32_t n_cases, const int32_t *d_ev, double *d_lp,
+                                     double *d_post, int32_t *d_st, void *stream) {
+  if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
+  if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
+  if (n_cases == 0) return JT_OK;
+  if (!d_ev || !d_lp || !d_post || !d_st) { set_error("null buffer"); return JT_EINVAL; }
+  std::lock_guard<std::mutex> lk(pl->mu);
+  JT_CUDA_TRY(cudaSetDevice(pl->device));
+  const int W = pl->P.tile;
+  jt_status st = ensure_default_arena(pl, (n_cases + W - 1) / W);
+  if (st != JT_OK) return st;
+  cudaStream_t s = pick_stream(pl, stream);
+  const int64_t chunk = (int64_t)pl->arena.tiles * W;
+  for (int64_t b = 0; b < n_cases; b += chunk) {
+    const int32_t nc = (int32_t)std::min<int64_t>(chunk, n_cases - b);
+    st = run_chunk(pl, pl->arena, d_ev + b * pl->P.n, nc, d_lp + b, d_post + b * pl->P.sum_card, d_st + b, s);
+    if (st != JT_OK) return st;
+  }
+  return JT_OK;
+}
+
+static jt_status ensure_io(jt_plan *pl, int cases) {
+  if (pl->io_cases >= cases) return JT_OK;
+  free_io(pl);
+  const Plan &P = pl->P;
+  pl->io_ev = align_up(sizeof(int32_t) * (size_t)cases * P.n);
+  pl->io_lp = align_up(sizeof(double) * (size_t)cases);
+  pl->io_post = align_up(sizeof(double) * (size_t)cases * P.sum_card);
+  pl->io_st = align_up(sizeof(int32_t) * (size_t)cases);
+  const size_t bytes = pl->io_ev + pl->io_lp + pl->io_post + pl->io_st;
+  JT_CUDA_TRY(cudaMalloc(&pl->d_io, bytes));
+  JT_CUDA_TRY(cudaHostAlloc(&pl->h_io, bytes, cudaHostAllocDefault));
+  pl->io_cases = cases;
+  return JT_OK;
+}
+
+extern "C" jt_status jt_infer(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp, double *post,
+                              int32_t *cst, void *stream) {
+  if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
+  if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
+  if (n_cases == 0) return JT_OK;
+  if (!ev || !lp || !post || !cst) { set_error("null buffer"); return JT_EINVAL; }
+  std::lock_guard<std::mutex> lk(pl->mu);
+  JT_CUDA_TRY(cudaSetDevice(pl->device));
+  const Plan &P = pl->P;
+  const int W = P.tile;
+  jt_status st = ensure_default_arena(pl, (n_cases + W - 1) / W);
+  if (st != JT_OK) return st;
+  const int chunk = pl->arena.tiles * W;
+  st = ensure_io(pl, std::min<int>(chunk, n_cases));
+  if (st != JT_OK) return st;
+  cudaStream_t s = pick_stream(pl, stream);
+  char *d = static_cast<char *>(pl->d_io), *h = static_cast<char *>(pl->h_io);
+  int32_t *d_ev = reinterpret_cast<int32_t *>(d), *h_ev = reinterpret_cast<int32_t *>(h);
+  double *d_lp = reinterpret_cast<double *>(d + pl->io_ev), *h_lp = reinterpret_cast<double *>(h + pl->io_ev);
+  double *d_po = reinterpret_cast<double *>(d + pl->io_ev + pl->io_lp);
+  double *h_po = reinterpret_cast<double *>(h + pl->io_ev + pl->io_lp);
+  int32_t *d_st = reinterpret_cast<int32_t *>(d + pl->io_ev + pl->io_lp + pl->io_post);
+  int32_t *h_st = reinterpret_cast<int32_t *>(h + pl->io_ev + pl->io_lp + pl->io_post);
+  for (int64_t b = 0; b < n_cases; b += chunk) {
+    const int32_t nc = (int32_t)std::min<int64_t>(chunk, n_cases - b);
+    std::memcpy(h_ev, ev + b * P.n, sizeof(int32_t) * (size_t)nc * P.n);
+    JT_CUDA_TRY(cudaMemcpyAsync(d_ev, h_ev, sizeof(int32_t) * (size_t)nc * P.n, cudaMemcpyHostToDevice, s));
+    st = run_chunk(pl, pl->arena, d_ev, nc, d_lp, d_po, d_st, s);
+    if (st != JT_OK) return st;
+    JT_CUDA_TRY(cudaMemcpyAsync(h_lp, d_lp, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    JT_CUDA_TRY(cudaMemcpyAsync(h_po, d_po, sizeof(double) * (size_t)nc * P.sum_card, cudaMemcpyDeviceToHost, s));
+    JT_CUDA_TRY(cudaMemcpyAsync(h_st, d_st, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, s));
+    JT_CUDA_TRY(cudaStreamSynchronize(s));
+    std::memcpy(lp + b, h_lp, sizeof(double) * nc);
+    std::memcpy(post + b * P.sum_card, h_po, sizeof(double) * (size_t)nc * P.sum_card);
+    std::memcpy(cst + b, h_st, sizeof(int32_t) * nc);
+  }
+  return JT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plain FP64 per-case path
+// ---------------------------------------------------------------------------
+static jt_status ensure_plain(jt_plan *pl) {
+  if (pl->d_plain) return JT_OK;
+  const Plan &P = pl->P;
+  int64_t maxsep = 1;
+  for (auto &C : P.cl) maxsep = std::max(maxsep, C.nsep);
+  std::vector<char> blob;
+  std::vector<int32_t> card32(P.card.begin(), P.card.end());
+  const size_t o_b = put(blob, P.base64), o_pp = put(blob, P.ppool), o_card = put(blob, card32),
+               o_po = put(blob, P.post_off);
+  const size_t o_psi = align_up(blob.size());
+  const size_t o_sep = o_psi + align_up(sizeof(double) * P.sum_cl);
+  const size_t o_tmp = o_sep + align_up(sizeof(double) * P.sep_rows);
+  const size_t o_marg = o_tmp + align_up(sizeof(double) * maxsep);
+  const size_t o_pe = o_marg + align_up(sizeof(double) * P.sum_card);
+  const size_t o_ev = o_pe + align_up(sizeof(double));
+  const size_t total = o_ev + align_up(sizeof(int32_t) * P.n);
+  void *mem = nullptr;
+  if (cudaMalloc(&mem, total) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("plain path workspace allocation failed");
+    return JT_ENOMEM;
+  }
+  JT_CUDA_TRY(cudaMemcpy(mem, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  char *b = static_cast<char *>(mem);
+  pl->d_plain = mem;
+  pl->pw.base = reinterpret_cast<double *>(b + o_b);
+  pl->pw.pool = reinterpret_cast<int64_t *>(b + o_pp);
+  pl->pw.card = reinterpret_cast<int32_t *>(b + o_card);
+  pl->pw.post_off = reinterpret_cast<int64_t *>(b + o_po);
+  pl->pw.psi = reinterpret_cast<double *>(b + o_psi);
+  pl->pw.sep = reinterpret_cast<double *>(b + o_sep);
+  pl->pw.tmp = reinterpret_cast<double *>(b + o_tmp);
+  pl->pw.marg = reinterpret_cast<double *>(b + o_marg);
+  pl->pw.pe = reinterpret_cast<double *>(b + o_pe);
+  pl->pw.ev = reinterpret_cast<int32_t *>(b + o_ev);
+  return JT_OK;
+}
+
+static jt_status plain_case(jt_plan *pl, const int32_t *h_ev, double *d_lp, double *d_post, int32_t *d_st,
+                            cudaStream_t s) {
+  const Plan &P = pl->P;
+  const PlainWork &w = pl->pw;
+  JT_CUDA_TRY(cudaMemcpyAsync(w.ev, h_ev, sizeof(int32_t) * P.n, cudaMemcpyHostToDevice, s));
+  const int m = (int)P.cl.size();
+  // initialisation + reduction (evidence), one launch per clique
+  for (int c = 0; c < m; ++c)
+    launch_plain_init(w.psi + P.p_base_off[c], w.base + P.p_base_off[c], P.pmap[P.p_init_map[c]], w.pool, w.ev, s);
+  // collect: children before parents
+  for (int q = m - 1; q >= 1; --q) {
+    const int c = P.bfs[q], p = P.cl[c].parent;
+    double *sep = w.sep + P.p_sep_off[c];
+    JT_CUDA_TRY(cudaMemsetAsync(sep, 0, sizeof(double) * P.cl[c].nsep, s));
+    launch_plain_marg(w.psi + P.p_base_off[c], sep, P.pmap[P.p_child_map[c]], w.pool, s);
+    launch_plain_extend(w.psi + P.p_base_off[p], sep, P.pmap[P.p_parent_map[c]], w.pool, s);
+  }
+  JT_CUDA_TRY(cudaMemsetAsync(w.pe, 0, sizeof(double), s));
+  launch_plain_marg(w.psi + P.p_base_off[P.root], w.pe, P.pmap[P.p_root_map[0]], w.pool, s);
+  // distribute: parents before children
+  for (int q = 1; q < m; ++q) {
+    const int c = P.bfs[q], p = P.cl[c].parent;
+    const int64_t ns = P.cl[c].nsep;
+    JT_CUDA_TRY(cudaMemsetAsync(w.tmp, 0, sizeof(double) * ns, s));
+    launch_plain_marg(w.psi + P.p_base_off[p], w.tmp, P.pmap[P.p_parent_map[c]], w.pool, s);
+    launch_plain_divide(w.tmp, w.sep + P.p_sep_off[c], ns, s);
+    launch_plain_extend(w.psi + P.p_base_off[c], w.tmp, P.pmap[P.p_child_map[c]], w.pool, s);
+  }
+  JT_CUDA_TRY(cudaMemsetAsync(w.marg, 0, sizeof(double) * P.sum_card, s));
+  for (int v = 0; v < P.n; ++v) {
+    if (h_ev[v] >= 0) continue;
+    const int c = P.post_src[v];
+    launch_plain_marg(w.psi + P.p_base_off[c], w.marg + P.post_off[v], P.pmap[P.p_post_map[v]], w.pool, s);
+  }
+  launch_plain_finalize(w.pe, w.marg, w.ev, w.card, w.post_off, P.n, d_lp, d_post, d_st, s);
+  JT_CUDA_TRY(cudaGetLastError());
+  return JT_OK;
+}
+
+extern "C" jt_status jt_infer_plain(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp,
+                                    double *post, int32_t *cst, void *stream) {
+  if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
+  if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
+  if (n_cases == 0) return JT_OK;
+  if (!ev || !lp || !post || !cst) { set_error("null buffer"); return JT_EINVAL; }
+  std::lock_guard<std::mutex> lk(pl->mu);
+  JT_CUDA_TRY(cudaSetDevice(pl->device));
+  jt_status st = ensure_plain(pl);
+  if (st != JT_OK) return st;
+  const Plan &P = pl->P;
+  const int batch = 256;
+  st = ensure_io(pl, std::min<int>(batch, n_cases));
+  if (st != JT_OK) return st;
+  cudaStream_t s = pick_stream(pl, stream);
+  char *d = static_cast<char *>(pl->d_io);
+  double *d_lp = reinterpret_cast<double *>(d + pl->io_ev);
+  double *d_po = reinterpret_cast<double *>(d + pl->io_ev + pl->io_lp);
+  int32_t *d_st = reinterpret_cast<int32_t *>(d + pl->io_ev + pl->io_lp + pl->io_post);
+  for (int64_t b = 0; b < n_cases; b += batch) {
+    const int nb = (int)std::min<int64_t>(batch, n_cases - b);
+    for (int i = 0; i < nb; ++i) {
+      const int32_t *e = ev + (b + i) * P.n;
+      bool badev = false;
+      for (int v = 0; v < P.n; ++v)
+        if (e[v] < -1 || e[v] >= P.card[v]) badev = true;
+      if (badev) {
+        // flagged on the host; the device outputs of this slot are overwritten below
+        continue;
+      }
+      st = plain_case(pl, e, d_lp + i, d_po + (size_t)i * P.sum_card, d_st + i, s);
+      if (st != JT_OK) return st;
+    }
+    JT_CUDA_TRY(cudaMemcpyAsync(lp + b, d_lp, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    JT_CUDA_TRY(cudaMemcpyAsync(post + b * P.sum_card, d_po, sizeof(double) * (size_t)nb * P.sum_card,
+                                cudaMemcpyDeviceToHost, s));
+    JT_CUDA_TRY(cudaMemcpyAsync(cst + b, d_st, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
+    JT_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < nb; ++i) {
+      const int32_t *e = ev + (b + i) * P.n;
+      bool badev = false;
+      for (int v = 0; v < P.n; ++v)
+        if (e[v] < -1 || e[v] >= P.card[v]) badev = true;
+      if (badev) {
+        lp[b + i] = std::nan("");
+        cst[b + i] = JT_CASE_BAD_EVIDENCE;
+        for (int64_t k = 0; k < P.sum_card; ++k) post[(b + i) * P.sum_card + k] = std::nan("");
+      }
+    }
+  }
+  return JT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// instrumented run (per-kernel timing with CUDA events)
+// ---------------------------------------------------------------------------
+extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_ev, double *d_lp,
+                                double *d_post, int32_t *d_st, void *stream, double *out) {
+  if (!pl || n_cases <= 0 || !out) { set_error("bad argument"); return JT_EINVAL; }
+  if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
+  std::lock_guard<std::mutex> lk(pl->mu);
+  JT_CUDA_TRY(cudaSetDevice(pl->device));
+  const Plan &P = pl->P;
+  const int W = P.tile;
+  jt_status st = ensure_default_arena(pl, (n_cases + W - 1) / W);
+  if (st != JT_OK) return st;
+  cudaStream_t s = pick_stream(pl, stream);
+  const int64_t chunk = (int64_t)pl->arena.tiles * W;
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&]() {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    return (int)ev.size() - 1;
+  };
+  struct Span { int a, b, kind; };
+  std::vector<Span> spans;
+  const int start = mark();
+  for (int64_t b = 0; b < n_cases; b += chunk) {
+    const int32_t nc = (int32_t)std::min<int64_t>(chunk, n_cases - b);
+    DevArena A = pl->arena.da;
+    A.tiles = (nc + W - 1) / W;
+    JT_CUDA_TRY(cudaMemsetAsync(A.bad, 0, arena_layout(P).bad * (size_t)A.tiles, s));
+    int e0 = mark();
+    launch_evidence(P.cpt_per_thread, d_ev + b * P.n, nc, pl->dp, A, s);
+    spans.push_back({e0, mark(), 2});
+    JT_CUDA_TRY(cudaMemsetAsync(A.maxbits, 0, arena_layout(P).maxbits * (size_t)A.tiles, s));
+    for (int L = P.height; L >= 0; --L) {
+      const Level &lv = P.levels[L];
+      if (lv.c_item_end == lv.c_item_begin) continue;
+      int a = mark();
+      launch_collect(P.cpt_per_thread, pl->dp, A, lv.c_item_begin, lv.c_item_end - lv.c_item_begin,
+                     lv.c_max_maps, s);
+      spans.push_back({a, mark(), 0});
+    }
+    for (int L = 0; L <= P.height; ++L) {
+      const Level &lv = P.levels[L];
+      if (lv.d_item_end == lv.d_item_begin) continue;
+      int a = mark();
+      launch_distribute(P.cpt_per_thread, pl->dp, A, lv.d_item_begin, lv.d_item_end - lv.d_item_begin, s);
+      spans.push_back({a, mark(), 1});
+    }
+    int f0 = mark();
+    launch_finalize(P.cpt_per_thread, pl->dp, A, nc, P.dcl[P.root].sep_row, d_lp + b,
+                    d_post + b * P.sum_card, d_st + b, s);
+    spans.push_back({f0, mark(), 2});
+  }
+  const int stop = mark();
+  JT_CUDA_TRY(cudaGetLastError());
+  JT_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < 6; ++k) out[k] = 0;
+  for (const Span &sp : spans) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev[sp.a], ev[sp.b]);
+    out[sp.kind] += ms;
+    if (sp.kind < 2) out[3 + sp.kind] += 1;
+  }
+  float tot = 0;
+  cudaEventElapsedTime(&tot, ev[start], ev[stop]);
+  out[5] = tot;
+  for (auto e : ev) cudaEventDestroy(e);
+  return JT_OK;
+}

@@ -1,0 +1,694 @@
+// Host-side network compiler: BN -> junction tree -> device work description.
+//
+// Section 1 of the paper: a BN is converted into a secondary structure, the
+// junction tree, whose nodes (cliques) and edges (separators) carry
+// potential tables.  Section 2: the tree is traversed breadth-first and
+// every clique is tagged with its layer; a root-selection strategy keeps
+// the number of layers small; table operations are driven by index
+// mappings between the original and the updated table.  This file builds
+// all of that once per network:
+//   moral graph -> min-fill elimination -> maximal cliques -> maximum-weight
+//   spanning tree -> root -> BFS layers -> per-clique variable layout ->
+//   index maps of every table operation -> per-layer thread-block lists.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <tuple>
+
+#include "jt_internal.h"
+
+namespace jt {
+namespace {
+
+using Bits = std::vector<uint64_t>;
+
+inline bool bit(const Bits &b, int i) { return (b[i >> 6] >> (i & 63)) & 1ull; }
+inline void setbit(Bits &b, int i) { b[i >> 6] |= 1ull << (i & 63); }
+inline void clearbit(Bits &b, int i) { b[i >> 6] &= ~(1ull << (i & 63)); }
+
+int popcount_and(const Bits &a, const Bits &b) {
+  int k = 0;
+  for (size_t w = 0; w < a.size(); ++w) k += __builtin_popcountll(a[w] & b[w]);
+  return k;
+}
+
+bool subset_of(const Bits &a, const Bits &b) {
+  for (size_t w = 0; w < a.size(); ++w)
+    if (a[w] & ~b[w]) return false;
+  return true;
+}
+
+std::vector<int> members(const Bits &b, int n) {
+  std::vector<int> out;
+  for (int i = 0; i < n; ++i)
+    if (bit(b, i)) out.push_back(i);
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+jt_status validate(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
+                   const double *cpt, std::string &err) {
+  if (n <= 0 || !card || !pptr || !cpt) { err = "empty network or null array"; return JT_EINVAL; }
+  if (pptr[0] != 0) { err = "parent_ptr[0] must be 0"; return JT_EINVAL; }
+  for (int v = 0; v < n; ++v) {
+    if (card[v] < 2 || card[v] > (1 << 20)) { err = "card out of range at variable " + std::to_string(v); return JT_EINVAL; }
+    if (pptr[v + 1] < pptr[v]) { err = "parent_ptr not monotone"; return JT_EINVAL; }
+  }
+  if (pptr[n] > 0 && !par) { err = "null parents"; return JT_EINVAL; }
+  for (int v = 0; v < n; ++v) {
+    for (int k = pptr[v]; k < pptr[v + 1]; ++k) {
+      int p = par[k];
+      if (p < 0 || p >= n || p == v) { err = "bad parent of variable " + std::to_string(v); return JT_EINVAL; }
+      for (int q = pptr[v]; q < k; ++q)
+        if (par[q] == p) { err = "duplicate parent of variable " + std::to_string(v); return JT_EINVAL; }
+    }
+  }
+  // Kahn's algorithm: every node must be removable
+  std::vector<int> indeg(n, 0);
+  std::vector<std::vector<int>> kids(n);
+  for (int v = 0; v < n; ++v)
+    for (int k = pptr[v]; k < pptr[v + 1]; ++k) { kids[par[k]].push_back(v); ++indeg[v]; }
+  std::vector<int> stack;
+  for (int v = 0; v < n; ++v)
+    if (!indeg[v]) stack.push_back(v);
+  int seen = 0;
+  while (!stack.empty()) {
+    int v = stack.back();
+    stack.pop_back();
+    ++seen;
+    for (int c : kids[v])
+      if (--indeg[c] == 0) stack.push_back(c);
+  }
+  if (seen != n) { err = "parent graph has a directed cycle"; return JT_ECYCLE; }
+  // CPT rows
+  int64_t off = 0;
+  for (int v = 0; v < n; ++v) {
+    double rows = 1;
+    for (int k = pptr[v]; k < pptr[v + 1]; ++k) rows *= card[par[k]];
+    if (rows * card[v] > 2147483647.0) { err = "CPT of variable " + std::to_string(v) + " too large"; return JT_ETOOBIG; }
+    for (int64_t r = 0; r < (int64_t)rows; ++r) {
+      double s = 0;
+      for (int x = 0; x < card[v]; ++x) {
+        double p = cpt[off + r * card[v] + x];
+        if (!(p >= 0.0) || !std::isfinite(p)) {
+          err = "negative or non-finite CPT entry of variable " + std::to_string(v);
+          return JT_EINVAL;
+        }
+        s += p;
+      }
+      if (std::fabs(s - 1.0) > 1e-6) {
+        err = "CPT row of variable " + std::to_string(v) + " does not sum to 1";
+        return JT_EINVAL;
+      }
+    }
+    off += (int64_t)rows * card[v];
+  }
+  return JT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// triangulation and clique tree
+// ---------------------------------------------------------------------------
+
+// Min-fill elimination (fill = number of missing edges among the current
+// neighbours; ties to the lowest variable id).  Returns the maximal
+// elimination cliques in order of creation.
+std::vector<Bits> eliminate_min_fill(int n, std::vector<Bits> adj) {
+  const int W = (n + 63) / 64;
+  Bits alive(W, 0);
+  for (int v = 0; v < n; ++v) setbit(alive, v);
+  std::vector<Bits> kept;
+  std::vector<int64_t> fill(n, 0);
+  std::vector<char> dirty(n, 1);
+  auto compute_fill = [&](int v) {
+    std::vector<int> nb = members(adj[v], n);
+    int64_t present = 0;  // ordered pairs (a, b) of adjacent neighbours
+    for (int a : nb) present += popcount_and(adj[a], adj[v]);
+    int64_t d = (int64_t)nb.size();
+    return d * (d - 1) / 2 - present / 2;
+  };
+  for (int step = 0; step < n; ++step) {
+    int best = -1;
+    for (int v = 0; v < n; ++v) {
+      if (!bit(alive, v)) continue;
+      if (dirty[v]) { fill[v] = compute_fill(v); dirty[v] = 0; }
+      if (best < 0 || fill[v] < fill[best]) best = v;
+    }
+    const int v = best;
+    std::vector<int> nb = members(adj[v], n);
+    Bits clique = adj[v];
+    setbit(clique, v);
+    // connect the neighbours pairwise, then drop v
+    for (int a : nb) {
+      for (int b : nb)
+        if (a != b) setbit(adj[a], b);
+      clearbit(adj[a], v);
+    }
+    clearbit(alive, v);
+    adj[v].assign(W, 0);
+    // fill scores change only within distance two of v
+    for (int a : nb) {
+      dirty[a] = 1;
+      for (int b = 0; b < n; ++b)
+        if (bit(adj[a], b)) dirty[b] = 1;
+    }
+    bool maximal = true;
+    for (const Bits &k : kept)
+      if (subset_of(clique, k)) { maximal = false; break; }
+    if (maximal) kept.push_back(clique);
+  }
+  return kept;
+}
+
+struct Tree {
+  std::vector<std::vector<int>> nbr;
+};
+
+// Kruskal maximum-weight spanning tree over all clique pairs, weight = the
+// number of shared variables (zero allowed: components join by empty
+// separators); ties by (i, j).
+Tree spanning_tree(const std::vector<Bits> &cl) {
+  const int m = (int)cl.size();
+  std::vector<std::tuple<int, int, int>> edges;  // (-w, i, j)
+  edges.reserve((size_t)m * (m - 1) / 2);
+  for (int i = 0; i < m; ++i)
+    for (int j = i + 1; j < m; ++j) edges.emplace_back(-popcount_and(cl[i], cl[j]), i, j);
+  std::sort(edges.begin(), edges.end());
+  std::vector<int> uf(m);
+  std::iota(uf.begin(), uf.end(), 0);
+  auto find = [&](int a) {
+    while (uf[a] != a) { uf[a] = uf[uf[a]]; a = uf[a]; }
+    return a;
+  };
+  Tree t;
+  t.nbr.resize(m);
+  int joined = 0;
+  for (auto &e : edges) {
+    if (joined == m - 1) break;
+    int i = std::get<1>(e), j = std::get<2>(e);
+    int a = find(i), b = find(j);
+    if (a == b) continue;
+    uf[a] = b;
+    t.nbr[i].push_back(j);
+    t.nbr[j].push_back(i);
+    ++joined;
+  }
+  for (auto &v : t.nbr) std::sort(v.begin(), v.end());
+  return t;
+}
+
+std::vector<int> bfs_dist(const Tree &t, int s) {
+  std::vector<int> d(t.nbr.size(), -1);
+  std::queue<int> q;
+  q.push(s);
+  d[s] = 0;
+  while (!q.empty()) {
+    int a = q.front();
+    q.pop();
+    for (int b : t.nbr[a])
+      if (d[b] < 0) { d[b] = d[a] + 1; q.push(b); }
+  }
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// layout helpers
+// ---------------------------------------------------------------------------
+
+// Table of weights over an ordered variable list (last fastest): for every
+// entry of the mixed-radix space of `vars`, sum_i digit_i * weight[i].
+void linear_table(const std::vector<int> &cards, const std::vector<int64_t> &weight,
+                  std::vector<int32_t> &out) {
+  int64_t size = 1;
+  for (int c : cards) size *= c;
+  out.assign(size, 0);
+  const int k = (int)cards.size();
+  std::vector<int> dig(k, 0);
+  int64_t acc = 0;
+  for (int64_t e = 0; e < size; ++e) {
+    out[e] = (int32_t)acc;
+    for (int i = k - 1; i >= 0; --i) {
+      ++dig[i];
+      acc += weight[i];
+      if (dig[i] < cards[i]) break;
+      acc -= weight[i] * cards[i];
+      dig[i] = 0;
+    }
+  }
+}
+
+int64_t append_pool(std::vector<int32_t> &pool, const std::vector<int32_t> &t) {
+  int64_t off = (int64_t)pool.size();
+  pool.insert(pool.end(), t.begin(), t.end());
+  return off;
+}
+
+bool all_zero(const std::vector<int64_t> &w) {
+  for (auto x : w)
+    if (x) return false;
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// build_plan
+// ---------------------------------------------------------------------------
+jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
+                     const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err) {
+  jt_status st = validate(n, card, pptr, par, cpt, err);
+  if (st != JT_OK) return st;
+  P.opts = opts;
+  P.n = n;
+  P.card.assign(card, card + n);
+  P.pptr.assign(pptr, pptr + n + 1);
+  P.par.assign(par, par + pptr[n]);
+  P.cpt_off.assign(n + 1, 0);
+  for (int v = 0; v < n; ++v) {
+    int64_t rows = 1;
+    for (int k = pptr[v]; k < pptr[v + 1]; ++k) rows *= card[par[k]];
+    P.cpt_off[v + 1] = P.cpt_off[v] + rows * card[v];
+  }
+  P.cpt.assign(cpt, cpt + P.cpt_off[n]);
+  P.post_off.assign(n, 0);
+  P.sum_card = 0;
+  for (int v = 0; v < n; ++v) { P.post_off[v] = P.sum_card; P.sum_card += card[v]; }
+
+  // moral graph
+  const int W = (n + 63) / 64;
+  std::vector<Bits> adj(n, Bits(W, 0));
+  for (int v = 0; v < n; ++v) {
+    for (int k = pptr[v]; k < pptr[v + 1]; ++k) {
+      int p = par[k];
+      setbit(adj[v], p);
+      setbit(adj[p], v);
+      for (int q = k + 1; q < pptr[v + 1]; ++q) {
+        setbit(adj[p], par[q]);
+        setbit(adj[par[q]], p);
+      }
+    }
+  }
+  std::vector<Bits> cbits = eliminate_min_fill(n, adj);
+  const int m = (int)cbits.size();
+  const int64_t max_entries = opts.max_clique_entries > 0 ? opts.max_clique_entries : 2147483647LL;
+  P.cl.assign(m, HostClique());
+  std::vector<double> csize(m, 1.0);
+  for (int c = 0; c < m; ++c) {
+    for (int v : members(cbits[c], n)) csize[c] *= card[v];
+    if (csize[c] > (double)max_entries) {
+      err = "clique " + std::to_string(c) + " has " + std::to_string(csize[c]) + " entries";
+      return JT_ETOOBIG;
+    }
+  }
+  Tree tree = spanning_tree(cbits);
+
+  // root
+  int root = 0;
+  if (opts.root_rule == JT_ROOT_LARGEST) {
+    for (int c = 1; c < m; ++c)
+      if (csize[c] > csize[root]) root = c;
+  } else {
+    int best = -1;
+    for (int s = 0; s < m; ++s) {
+      std::vector<int> d = bfs_dist(tree, s);
+      int ecc = *std::max_element(d.begin(), d.end());
+      if (best < 0 || ecc < best || (ecc == best && csize[s] > csize[root])) {
+        best = ecc;
+        root = s;
+      }
+    }
+  }
+  P.root = root;
+
+  // orient: BFS from the root, neighbours ascending
+  std::vector<int> parent(m, -2), depth(m, 0);
+  P.bfs.clear();
+  P.bfs.push_back(root);
+  parent[root] = -1;
+  for (size_t h = 0; h < P.bfs.size(); ++h) {
+    int a = P.bfs[h];
+    for (int b : tree.nbr[a])
+      if (parent[b] == -2) {
+        parent[b] = a;
+        depth[b] = depth[a] + 1;
+        P.bfs.push_back(b);
+      }
+  }
+  P.height = 0;
+  for (int c = 0; c < m; ++c) P.height = std::max(P.height, depth[c]);
+
+  // variable layout: upward separator first (in the parent's order), then
+  // the remaining variables in ascending id
+  for (int c : P.bfs) {
+    HostClique &C = P.cl[c];
+    C.parent = parent[c];
+    C.depth = depth[c];
+    C.vars.clear();
+    if (C.parent >= 0)
+      for (int v : P.cl[C.parent].vars)
+        if (bit(cbits[c], v)) C.vars.push_back(v);
+    C.n_up = (int)C.vars.size();
+    for (int v = 0; v < n; ++v)
+      if (bit(cbits[c], v) && std::find(C.vars.begin(), C.vars.begin() + C.n_up, v) == C.vars.begin() + C.n_up)
+        C.vars.push_back(v);
+    const int k = (int)C.vars.size();
+    C.card.resize(k);
+    C.stride.resize(k);
+    int64_t s = 1;
+    for (int i = k - 1; i >= 0; --i) {
+      C.card[i] = card[C.vars[i]];
+      C.stride[i] = s;
+      s *= C.card[i];
+    }
+    C.size = s;
+    C.nsep = 1;
+    for (int i = 0; i < C.n_up; ++i) C.nsep *= C.card[i];
+    C.R = C.size / C.nsep;
+    if (C.parent >= 0) P.cl[C.parent].children.push_back(c);
+  }
+  for (auto &C : P.cl) std::sort(C.children.begin(), C.children.end());
+
+  // CPT assignment (smallest clique containing the family, lowest id on
+  // ties); posterior owner (smallest clique containing the variable)
+  P.assign.assign(n, -1);
+  P.post_src.assign(n, -1);
+  for (int v = 0; v < n; ++v) {
+    Bits fam(W, 0);
+    setbit(fam, v);
+    for (int k = pptr[v]; k < pptr[v + 1]; ++k) setbit(fam, par[k]);
+    for (int c = 0; c < m; ++c) {
+      if (bit(cbits[c], v) && (P.post_src[v] < 0 || csize[c] < csize[P.post_src[v]])) P.post_src[v] = c;
+      if (subset_of(fam, cbits[c]) && (P.assign[v] < 0 || csize[c] < csize[P.assign[v]])) P.assign[v] = c;
+    }
+    if (P.assign[v] < 0) { err = "internal: no clique covers a family"; return JT_EINVAL; }
+    P.cl[P.assign[v]].homed.push_back(v);
+    P.cl[P.post_src[v]].owned.push_back(v);
+  }
+
+  P.sum_cl = P.max_cl = P.sum_sep = 0;
+  for (int c = 0; c < m; ++c) {
+    P.sum_cl += P.cl[c].size;
+    P.max_cl = std::max(P.max_cl, P.cl[c].size);
+    if (c != root) P.sum_sep += P.cl[c].nsep;
+  }
+
+  // base tables: product of the assigned CPTs, in each clique's layout
+  P.base64.assign(P.sum_cl, 1.0);
+  P.base32.assign(P.sum_cl, 1.0f);
+  P.p_base_off.assign(m, 0);
+  std::vector<int64_t> psi_row(m, 0);
+  {
+    int64_t off = 0;
+    for (int c = 0; c < m; ++c) { P.p_base_off[c] = off; psi_row[c] = off; off += P.cl[c].size; }
+  }
+  for (int v = 0; v < n; ++v) {
+    const HostClique &C = P.cl[P.assign[v]];
+    // weight of each clique variable inside v's CPT (parents listed order, child fastest)
+    std::vector<int64_t> w(C.vars.size(), 0);
+    int64_t s = 1;
+    auto pos_of = [&](int x) { return (int)(std::find(C.vars.begin(), C.vars.end(), x) - C.vars.begin()); };
+    w[pos_of(v)] = s;
+    s *= card[v];
+    for (int k = pptr[v + 1] - 1; k >= pptr[v]; --k) {
+      w[pos_of(par[k])] = s;
+      s *= card[par[k]];
+    }
+    std::vector<int32_t> idx;
+    linear_table(C.card, w, idx);
+    double *b = P.base64.data() + P.p_base_off[P.assign[v]];
+    const double *t = P.cpt.data() + P.cpt_off[v];
+    for (int64_t e = 0; e < C.size; ++e) b[e] *= t[idx[e]];
+  }
+  // FP32 copy, each clique scaled by a power of two so that its maximum is
+  // in [1, 2); the exponents are a per-plan constant added to log P(e)
+  std::vector<int> base_exp(m, 0);
+  for (int c = 0; c < m; ++c) {
+    const double *b = P.base64.data() + P.p_base_off[c];
+    double mx = 0;
+    for (int64_t e = 0; e < P.cl[c].size; ++e) mx = std::max(mx, b[e]);
+    int ex = 0;
+    if (mx > 0) { std::frexp(mx, &ex); ex -= 1; }
+    base_exp[c] = ex;
+    for (int64_t e = 0; e < P.cl[c].size; ++e)
+      P.base32[P.p_base_off[c] + e] = (float)std::ldexp(b[e], -ex);
+  }
+
+  // ---------------------------------------------------------------------
+  // device descriptors
+  // ---------------------------------------------------------------------
+  P.ipool.clear();
+  P.dcl.assign(m, DClique{});
+  P.dmap.clear();
+  P.dtask.clear();
+  int64_t zero_len = 1;
+  for (int c = 0; c < m; ++c) zero_len = std::max({zero_len, P.cl[c].nsep, P.cl[c].R, P.cl[c].size});
+  // one shared all-zero table serves every map part that no variable feeds
+  const int64_t zero_off = 0;
+  P.ipool.assign(zero_len, 0);
+
+  std::vector<int64_t> sep_row(m, 0);
+  {
+    int64_t r = 0;
+    for (int c = 0; c < m; ++c) { sep_row[c] = r; r += P.cl[c].nsep; }
+    P.sep_rows = r;
+  }
+
+  auto table_or_zero = [&](const std::vector<int> &cards, const std::vector<int64_t> &w) -> int64_t {
+    if (all_zero(w)) return zero_off;
+    std::vector<int32_t> t;
+    linear_table(cards, w, t);
+    return append_pool(P.ipool, t);
+  };
+
+  for (int c = 0; c < m; ++c) {
+    HostClique &C = P.cl[c];
+    DClique &D = P.dcl[c];
+    D.psi_row = psi_row[c];
+    D.nsep = C.nsep;
+    D.R = C.R;
+    D.base_off = P.p_base_off[c];
+    D.sep_row = sep_row[c];
+    D.parent = C.parent;
+    // Empty separators (disconnected parts of the network) split the tree
+    // into independent component trees: such a child sends no message to
+    // its parent, its own total enters log P(e) directly.
+    D.is_root = (c == root) || (C.n_up == 0);
+    D.map_begin = (int32_t)P.dmap.size();
+    std::vector<int> up_card(C.card.begin(), C.card.begin() + C.n_up);
+    std::vector<int> res_card(C.card.begin() + C.n_up, C.card.end());
+    // child messages
+    for (int ch : C.children) {
+      const HostClique &K = P.cl[ch];
+      if (K.n_up == 0) continue;
+      // stride of each separator variable in the child's message (K's up block)
+      std::vector<int64_t> wa(C.n_up, 0), wb(C.vars.size() - C.n_up, 0);
+      for (int i = 0; i < K.n_up; ++i) {
+        int v = K.vars[i];
+        int64_t sstride = K.stride[i] / K.R;
+        int pos = (int)(std::find(C.vars.begin(), C.vars.end(), v) - C.vars.begin());
+        if (pos < C.n_up) wa[pos] = sstride; else wb[pos - C.n_up] = sstride;
+      }
+      DMap mp{};
+      mp.kind = MAP_CHILD;
+      mp.src = ch;
+      mp.src_row = sep_row[ch];
+      mp.A_off = table_or_zero(up_card, wa);
+      mp.B_off = table_or_zero(res_card, wb);
+      P.dmap.push_back(mp);
+    }
+    // evidence digits of the variables homed here
+    for (int v : C.homed) {
+      std::vector<int64_t> wa(C.n_up, 0), wb(C.vars.size() - C.n_up, 0);
+      int pos = (int)(std::find(C.vars.begin(), C.vars.end(), v) - C.vars.begin());
+      if (pos < C.n_up) wa[pos] = 1; else wb[pos - C.n_up] = 1;
+      DMap mp{};
+      mp.kind = MAP_EVIDENCE;
+      mp.src = v;
+      mp.src_row = 0;
+      mp.A_off = table_or_zero(up_card, wa);
+      mp.B_off = table_or_zero(res_card, wb);
+      P.dmap.push_back(mp);
+    }
+    D.map_end = (int32_t)P.dmap.size();
+  }
+  // distribute tasks: children first (ascending), then owned posteriors
+  std::vector<std::vector<int>> tasks_of(m);
+  for (int c = 0; c < m; ++c) {
+    const HostClique &C = P.cl[c];
+    auto make_task = [&](const std::vector<int> &target, int kind, int dst, int64_t dst_row) {
+      // target variables in C's layout order
+      std::vector<int> tpos, upos;
+      for (int i = 0; i < (int)C.vars.size(); ++i) {
+        bool in = std::find(target.begin(), target.end(), C.vars[i]) != target.end();
+        (in ? tpos : upos).push_back(i);
+      }
+      std::vector<int> tcard, ucard;
+      std::vector<int64_t> wa, wsa, wb, wsb;
+      for (int i : tpos) {
+        tcard.push_back(C.card[i]);
+        wa.push_back(C.stride[i]);
+        wsa.push_back(i < C.n_up ? C.stride[i] / C.R : 0);
+      }
+      for (int i : upos) {
+        ucard.push_back(C.card[i]);
+        wb.push_back(C.stride[i]);
+        wsb.push_back(i < C.n_up ? C.stride[i] / C.R : 0);
+      }
+      DTask t{};
+      t.T = 1;
+      for (int x : tcard) t.T *= x;
+      t.U = 1;
+      for (int x : ucard) t.U *= x;
+      t.A_off = table_or_zero(tcard, wa);
+      t.sA_off = table_or_zero(tcard, wsa);
+      t.B_off = table_or_zero(ucard, wb);
+      t.sB_off = table_or_zero(ucard, wsb);
+      t.clique = c;
+      t.kind = kind;
+      t.dst = dst;
+      t.dst_row = dst_row;
+      tasks_of[c].push_back((int)P.dtask.size());
+      P.dtask.push_back(t);
+    };
+    for (int ch : C.children) {
+      const HostClique &K = P.cl[ch];
+      if (K.n_up == 0) continue;
+      std::vector<int> sv(K.vars.begin(), K.vars.begin() + K.n_up);
+      make_task(sv, TASK_CHILD, ch, sep_row[ch]);
+    }
+    for (int v : C.owned) make_task(std::vector<int>{v}, TASK_POSTERIOR, v, P.post_off[v]);
+  }
+
+  // ---------------------------------------------------------------------
+  // per-layer thread-block lists
+  // ---------------------------------------------------------------------
+  const int NW = 8;  // warps per block
+  P.cpt_per_thread = opts.cases_per_thread > 0 ? opts.cases_per_thread : 4;
+  if (P.cpt_per_thread != 1 && P.cpt_per_thread != 2 && P.cpt_per_thread != 4) {
+    err = "cases_per_thread must be 1, 2 or 4";
+    return JT_EINVAL;
+  }
+  P.tile = 32 * P.cpt_per_thread;
+  P.rows_per_cta = opts.rows_per_cta > 0 ? opts.rows_per_cta : (P.cpt_per_thread == 4 ? 512 : 1024);
+  const int64_t ROWS = P.rows_per_cta;
+  P.citems.clear();
+  P.ditems.clear();
+  P.n_groups = 0;
+  P.n_partials = 0;
+  auto emit = [&](std::vector<DItem> &out, int task, int64_t nseg, int64_t rows) {
+    if (rows <= ROWS / NW) {
+      int64_t per = std::max<int64_t>(1, ROWS / rows);
+      for (int64_t t0 = 0; t0 < nseg; t0 += per) {
+        DItem it{};
+        it.t0 = t0;
+        it.nt = std::min(per, nseg - t0);
+        it.u0 = 0;
+        it.nu = rows;
+        it.task = task;
+        it.split = 0;
+        it.npieces = 1;
+        it.piece = 0;
+        it.group = -1;
+        it.partial = -1;
+        out.push_back(it);
+      }
+    } else {
+      int64_t np = (rows + ROWS - 1) / ROWS;
+      int64_t per = (rows + np - 1) / np;
+      np = (rows + per - 1) / per;
+      for (int64_t s = 0; s < nseg; ++s) {
+        int32_t group = -1, first = -1;
+        if (np > 1) {
+          group = (int32_t)P.n_groups++;
+          first = (int32_t)P.n_partials;
+          P.n_partials += np;
+        }
+        for (int64_t p = 0; p < np; ++p) {
+          DItem it{};
+          it.t0 = s;
+          it.nt = 1;
+          it.u0 = p * per;
+          it.nu = std::min(per, rows - p * per);
+          it.task = task;
+          it.split = 1;
+          it.npieces = (int32_t)np;
+          it.piece = (int32_t)p;
+          it.group = group;
+          it.partial = np > 1 ? first + (int32_t)p : -1;
+          out.push_back(it);
+        }
+      }
+    }
+  };
+  P.levels.assign(P.height + 1, Level{});
+  for (int L = 0; L <= P.height; ++L) {
+    Level &lv = P.levels[L];
+    lv.c_item_begin = (int64_t)P.citems.size();
+    for (int c = 0; c < m; ++c) {
+      if (P.cl[c].depth != L) continue;
+      emit(P.citems, c, P.cl[c].nsep, P.cl[c].R);
+      lv.c_max_maps = std::max(lv.c_max_maps, P.dcl[c].map_end - P.dcl[c].map_begin);
+    }
+    lv.c_item_end = (int64_t)P.citems.size();
+    lv.d_item_begin = (int64_t)P.ditems.size();
+    for (int c = 0; c < m; ++c) {
+      if (P.cl[c].depth != L) continue;
+      for (int t : tasks_of[c]) emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U);
+    }
+    lv.d_item_end = (int64_t)P.ditems.size();
+  }
+  P.base_exp_sum = 0;
+  for (int c = 0; c < m; ++c) P.base_exp_sum += base_exp[c];
+
+  // ---------------------------------------------------------------------
+  // plain FP64 path maps: (var, card, src stride, dst stride) quadruples
+  // ---------------------------------------------------------------------
+  P.pmap.clear();
+  P.ppool.clear();
+  auto plain_map = [&](const HostClique &X, const std::vector<int> &dst_vars) -> int {
+    // dst is row-major over dst_vars (last fastest)
+    DPlainMap pm{};
+    pm.size = X.size;
+    pm.nv = (int32_t)X.vars.size();
+    pm.var_off = (int64_t)P.ppool.size();
+    for (int i = 0; i < (int)X.vars.size(); ++i) {
+      int64_t ds = 0, s = 1;
+      for (int j = (int)dst_vars.size() - 1; j >= 0; --j) {
+        if (dst_vars[j] == X.vars[i]) ds = s;
+        s *= card[dst_vars[j]];
+      }
+      P.ppool.push_back(X.vars[i]);
+      P.ppool.push_back(X.card[i]);
+      P.ppool.push_back(X.stride[i]);
+      P.ppool.push_back(ds);
+    }
+    P.pmap.push_back(pm);
+    return (int)P.pmap.size() - 1;
+  };
+  P.p_child_map.assign(m, -1);
+  P.p_parent_map.assign(m, -1);
+  P.p_init_map.assign(m, -1);
+  P.p_post_map.assign(n, -1);
+  P.p_sep_off.assign(m, 0);
+  {
+    int64_t off = 0;
+    for (int c = 0; c < m; ++c) { P.p_sep_off[c] = off; off += P.cl[c].nsep; }
+  }
+  for (int c = 0; c < m; ++c) {
+    const HostClique &C = P.cl[c];
+    P.p_init_map[c] = plain_map(C, std::vector<int>{});
+    if (c == root) continue;
+    std::vector<int> sv(C.vars.begin(), C.vars.begin() + C.n_up);
+    P.p_child_map[c] = plain_map(C, sv);
+    P.p_parent_map[c] = plain_map(P.cl[C.parent], sv);
+  }
+  P.p_root_map.assign(1, plain_map(P.cl[root], std::vector<int>{}));
+  for (int v = 0; v < n; ++v) P.p_post_map[v] = plain_map(P.cl[P.post_src[v]], std::vector<int>{v});
+  return JT_OK;
+}
+
+}  // namespace jt

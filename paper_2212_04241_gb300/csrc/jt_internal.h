@@ -1,0 +1,164 @@
+// Internal structures shared by the host compiler, the runtime and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/jt.h"
+
+namespace jt {
+
+// ---------------------------------------------------------------------------
+// Device descriptors (plain old data, copied to the device once per plan)
+// ---------------------------------------------------------------------------
+
+// A clique for the collect pass.  Its table is laid out with the upward
+// separator's variables outermost, so entry e = s*R + u with s the separator
+// entry (segment) and u the row inside the segment.
+struct DClique {
+  int64_t psi_row;    // first row of this clique inside a tile's psi region
+  int64_t nsep;       // |S_up| (1 for the root)
+  int64_t R;          // |C| / |S_up|
+  int64_t base_off;   // offset into the FP32 base-table pool
+  int64_t sep_row;    // first row of its upward message inside a tile's sep region
+  int32_t map_begin;  // collect maps [map_begin, map_end)
+  int32_t map_end;
+  int32_t parent;     // -1 for the root
+  int32_t is_root;    // 1 for a component root: the tree root, or a clique
+                      // whose separator towards its parent is empty
+};
+
+// A linear index map over a clique's entries: idx(s*R + u) = A[s] + B[u].
+//   kind MAP_CHILD: idx is the entry of child clique `src`'s upward message
+//   kind MAP_EVIDENCE: idx is the state of variable `src` (evidence test)
+enum { MAP_CHILD = 0, MAP_EVIDENCE = 1 };
+struct DMap {
+  int64_t A_off;      // int32 pool offset, nsep entries
+  int64_t B_off;      // int32 pool offset, R entries
+  int64_t src_row;    // MAP_CHILD: child's sep_row
+  int32_t kind;
+  int32_t src;        // child clique / variable
+};
+
+// A distribute target of a clique: for t in [0, T),
+//   value(t) = sum_{u < U} psi[A[t] + B[u]] * rho[sA[t] + sB[u]]
+// where rho is the clique's own upward ratio (a component root uses 2^-k).
+//   kind TASK_CHILD: writes rho_child[t] = value(t) / phistar_child[t]
+//   kind TASK_POSTERIOR: writes the unnormalised marginal of variable dst
+enum { TASK_CHILD = 0, TASK_POSTERIOR = 1 };
+struct DTask {
+  int64_t T, U;
+  int64_t A_off, B_off, sA_off, sB_off;  // int32 pool offsets
+  int64_t dst_row;    // TASK_CHILD: child's sep_row; TASK_POSTERIOR: row in the posterior region
+  int32_t clique;     // source clique
+  int32_t kind;
+  int32_t dst;        // child clique / variable
+  int32_t pad;
+};
+
+// One thread block of a layer launch (the same list serves every tile).
+//   split == 0: the block owns segments [t0, t0+nt), one warp per segment
+//   split == 1: the block owns rows [u0, u0+nu) of segment t0; when the
+//               segment has several pieces, the block writes a partial sum
+//               and the last piece to finish combines them in piece order
+struct DItem {
+  int64_t t0, nt;
+  int64_t u0, nu;
+  int32_t task;       // clique (collect) or task (distribute)
+  int32_t split;
+  int32_t npieces;
+  int32_t piece;
+  int32_t group;      // split group (counter index), -1 if npieces == 1
+  int32_t partial;    // partial-sum slot of this piece
+};
+
+// Plain FP64 path: descriptor of a mixed-radix mapping from the entries of a
+// source table onto a target table (one thread per source entry).
+struct DPlainMap {
+  int64_t size;       // source entries
+  int64_t var_off;    // offset into the int64 plain pool: nv triples (card, src stride, dst stride)
+  int32_t nv;
+  int32_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// Host plan
+// ---------------------------------------------------------------------------
+
+struct HostClique {
+  std::vector<int> vars;        // layout order: upward separator first
+  std::vector<int> card;
+  std::vector<int64_t> stride;  // stride of vars[i] in this table (last fastest)
+  int64_t size = 1;
+  int n_up = 0;                 // number of upward-separator variables
+  int64_t nsep = 1, R = 1;
+  int parent = -1, depth = 0;
+  std::vector<int> children;
+  std::vector<int> homed;       // variables whose evidence this clique applies
+  std::vector<int> owned;       // variables whose posterior this clique provides
+};
+
+struct Level {
+  // collect and distribute work of one tree layer
+  int64_t c_item_begin = 0, c_item_end = 0;   // into collect_items
+  int64_t d_item_begin = 0, d_item_end = 0;   // into distribute_items
+  int c_max_maps = 0;                          // most maps of a clique in the layer
+};
+
+struct Plan {
+  // network
+  int n = 0;
+  std::vector<int> card;
+  std::vector<int> pptr, par;
+  std::vector<double> cpt;
+  std::vector<int64_t> cpt_off;
+  std::vector<int64_t> post_off;  // per variable, offset into a posterior row
+  int64_t sum_card = 0;
+
+  // tree
+  std::vector<HostClique> cl;
+  int root = 0;
+  int height = 0;
+  std::vector<int> bfs;           // BFS order from the root
+  std::vector<int> assign;        // CPT v -> clique
+  std::vector<int> post_src;      // variable -> clique that owns its posterior
+  int64_t sum_cl = 0, max_cl = 0, sum_sep = 0;
+
+  // device-side description (host copies)
+  std::vector<DClique> dcl;
+  std::vector<DMap> dmap;
+  std::vector<DTask> dtask;
+  std::vector<DItem> citems, ditems;
+  std::vector<Level> levels;      // index = depth
+  std::vector<int32_t> ipool;     // int32 index tables
+  std::vector<float> base32;
+  std::vector<double> base64;
+  int64_t sep_rows = 0;           // rows of a tile's sep region (sum of nsep incl. root)
+  int64_t n_groups = 0, n_partials = 0;
+  int32_t base_exp_sum = 0;       // sum of the FP32 base-table power-of-two exponents
+
+  // plain path
+  std::vector<DPlainMap> pmap;
+  std::vector<int64_t> ppool;
+  std::vector<int> p_child_map;   // per clique: child entries -> its separator
+  std::vector<int> p_parent_map;  // per clique: parent entries -> its separator
+  std::vector<int> p_post_map;    // per variable: owner entries -> the variable
+  std::vector<int> p_root_map;    // root entries -> scalar (size 1)
+  std::vector<int> p_init_map;    // per clique: entries -> (unused dst), digit decode
+  std::vector<int64_t> p_base_off;  // per clique, offset in base64 / plain psi
+  std::vector<int64_t> p_sep_off;   // per clique, offset in plain sep arrays
+
+  jt_compile_opts opts{};
+  int cpt_per_thread = 4;
+  int tile = 128;
+  int rows_per_cta = 2048;
+};
+
+// compile.cpp
+jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
+                     const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err);
+
+void set_error(const std::string &msg);
+
+}  // namespace jt

@@ -1,0 +1,76 @@
+// Device-side views of a plan and of a batch arena, shared by the kernels and the runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "jt_internal.h"
+
+namespace jt {
+
+constexpr int kWarps = 8;               // warps per thread block of a layer launch
+constexpr int kThreads = 32 * kWarps;
+
+struct DevPlan {
+  const DClique *cl;
+  const DMap *maps;
+  const DTask *tasks;
+  const DItem *citems;
+  const DItem *ditems;
+  const int32_t *ipool;
+  const float *base32;
+  const int32_t *card;       // [n]
+  const int64_t *post_off;   // [n]
+  int32_t n_vars;
+  int32_t n_cliques;
+  int32_t root;
+  int32_t base_exp_sum;      // sum over cliques of the base-table exponents
+  int64_t psi_rows;          // rows of one tile's psi region (sum |C|)
+  int64_t sep_rows;          // rows of one tile's message regions
+  int64_t post_rows;         // rows of one tile's posterior region (sum card)
+  int64_t n_partials;
+  int64_t n_groups;
+};
+
+// Per-batch device memory.  Row-major [tile][row][W] for the FP32 tables,
+// W = 32 * cases-per-thread consecutive evidence cases in a row.
+struct DevArena {
+  float *psi;          // collect-pass clique tables
+  float *phistar;      // collect messages (raw sums), one block of rows per clique
+  float *rho;          // distribute ratios phi** / phi*, same layout as phistar
+  float *post;         // unnormalised posterior marginals
+  float *partial;      // partial sums of split segments [tile][slot][W]
+  uint32_t *maxbits;   // [tile][clique][W] bit pattern of max psi (>= 0)
+  uint32_t *counters;  // [tile][group] pieces finished
+  int32_t *ev;         // [tile][var][W] evidence, -1 = unobserved
+  int32_t *bad;        // [tile * W] 1 = invalid evidence
+  int32_t tiles;       // tiles in this chunk
+};
+
+// launchers (kernels.cu)
+void launch_evidence(int cpt, const int32_t *d_ev_in, int32_t n_cases, const DevPlan &P,
+                     const DevArena &A, cudaStream_t s);
+void launch_collect(int cpt, const DevPlan &P, const DevArena &A, int64_t item_begin,
+                    int64_t n_items, int max_maps, cudaStream_t s);
+void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t item_begin,
+                       int64_t n_items, cudaStream_t s);
+void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cases,
+                     int64_t root_sep_row, double *d_log_pe, double *d_post, int32_t *d_status,
+                     cudaStream_t s);
+size_t collect_smem_bytes(int cpt, int max_maps);
+// raise the dynamic shared-memory limit of the collect kernel (once per plan)
+cudaError_t configure_collect_smem(int cpt, size_t bytes);
+constexpr int kMaxTilesPerChunk = 16384;
+
+// plain FP64 path
+void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,
+                       const int32_t *d_ev, cudaStream_t s);
+void launch_plain_marg(const double *src, double *dst, const DPlainMap &m, const int64_t *pool,
+                       cudaStream_t s);
+void launch_plain_extend(double *x, const double *y, const DPlainMap &m, const int64_t *pool,
+                         cudaStream_t s);
+void launch_plain_divide(double *num, const double *den, int64_t n, cudaStream_t s);
+void launch_plain_finalize(const double *pe, const double *marg, const int32_t *d_ev,
+                           const int32_t *card, const int64_t *post_off, int32_t n_vars,
+                           double *d_log_pe, double *d_post, int32_t *d_status, cudaStream_t s);
+
+}  // namespace jt

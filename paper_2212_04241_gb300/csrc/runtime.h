@@ -1,0 +1,68 @@
+// Runtime objects behind the opaque jt_plan handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace jt {
+
+// Bytes of one case tile in each arena region.
+struct ArenaLayout {
+  size_t psi, sep, post, partial, maxbits, counters, ev, bad;
+  size_t per_tile;
+};
+
+// Device memory for the per-batch tables of up to `tiles` case tiles, and
+// the CUDA graphs captured against it (one per tile count).
+struct Arena {
+  void *mem = nullptr;
+  size_t bytes = 0;
+  int tiles = 0;
+  bool owns = true;
+  DevArena da{};
+  std::map<int, cudaGraphExec_t> graphs;
+};
+
+struct PlainWork {
+  double *base = nullptr, *psi = nullptr, *sep = nullptr, *tmp = nullptr, *marg = nullptr, *pe = nullptr;
+  int64_t *pool = nullptr, *post_off = nullptr;
+  int32_t *card = nullptr, *ev = nullptr;
+};
+
+ArenaLayout arena_layout(const Plan &P);
+jt_status arena_alloc(const Plan &P, Arena &a, int tiles);
+jt_status arena_wrap(const Plan &P, Arena &a, void *mem, size_t bytes, int tiles);
+void arena_free(Arena &a);
+
+}  // namespace jt
+
+struct jt_plan {
+  jt::Plan P;
+  bool host_only = false;
+  int device = 0;
+  cudaStream_t stream = nullptr;          // default stream of the plan
+  cudaStream_t capture_stream = nullptr;  // private stream for graph capture
+  void *d_static = nullptr;
+  size_t static_bytes = 0;
+  jt::DevPlan dp{};
+  jt::Arena arena;                        // default arena of jt_infer / jt_infer_device
+  int budget_tiles_cache = 0;
+  // staging for host-buffer calls
+  void *d_io = nullptr, *h_io = nullptr;
+  size_t io_ev = 0, io_lp = 0, io_post = 0, io_st = 0;
+  int io_cases = 0;
+  // plain FP64 path
+  void *d_plain = nullptr;
+  jt::PlainWork pw;
+  std::mutex mu;
+};
+
+namespace jt {
+jt_status run_chunk(jt_plan *pl, Arena &a, const int32_t *d_ev, int32_t nc, double *d_lp, double *d_post,
+                    int32_t *d_st, cudaStream_t s);
+int budget_tiles(const jt_plan *pl, int64_t budget_bytes);
+}  // namespace jt

@@ -47,3 +47,15 @@ def max_logpe_err(a, b):
     if not ok.any():
         return 0.0
     return float(np.max(np.abs(a[ok] - b[ok]) / np.maximum(1.0, np.abs(b[ok]))))
+
+
+def assert_parity32(lp, post, st, olp, opost, ost, where=""):
+    """FP32 batched path vs FP64 oracle: statuses equal, max abs posterior
+    error <= 1e-5, |d log P(e)| <= 1e-6 * max(1, |log P(e)|)."""
+    assert np.array_equal(st, ost), f"{where}: status mismatch"
+    ok = ost == 0
+    perr = float(np.max(np.abs(post[ok] - opost[ok]))) if ok.any() else 0.0
+    lerr = max_logpe_err(lp[ok], olp[ok]) if ok.any() else 0.0
+    assert perr <= POST_TOL32, f"{where}: posterior error {perr:.3g}"
+    assert lerr <= LOGPE_REL32, f"{where}: log P(e) error {lerr:.3g}"
+    return perr, lerr

@@ -1,0 +1,120 @@
+"""The library's host compiler (jt_compile with host_only=1), CPU only.
+
+Checks the junction-tree properties of the plan it builds and compares its
+clique set with the oracle's independently written compiler (both follow
+the same min-fill rule, so the maximal cliques must coincide as sets).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import configs
+from synth.bn import make_network, tiny_random_network
+import paper_2212_04241_gb300.jt as J
+
+
+def _plan(net, **kw):
+    return J.Plan(net, host_only=1, **kw)
+
+
+def _structure(p):
+    info = p.info()
+    return [p.clique(c) for c in range(info["n_cliques"])], info
+
+
+@pytest.mark.parametrize("name", ["bn20", "bn60", "bn110", "bn420", "bn1000"])
+def test_cliques_match_oracle(name):
+    net = configs.network(name)
+    cl, info = _structure(_plan(net))
+    o = oracle.Oracle(net)
+    ours = sorted(tuple(sorted(v)) for v, _, _ in cl)
+    theirs = sorted(tuple(v) for v, _ in o.cliques())
+    assert ours == theirs
+    assert info["max_clique_entries"] == o.max_clique
+    assert info["sum_clique_entries"] == o.sum_clique
+
+
+@pytest.mark.parametrize("name", ["bn20", "bn60", "bn110", "bn1000"])
+@pytest.mark.parametrize("root_rule", [J.JT_ROOT_LARGEST, J.JT_ROOT_MIN_HEIGHT])
+def test_junction_tree_properties(name, root_rule):
+    net = configs.network(name)
+    p = _plan(net, root_rule=root_rule)
+    cl, info = _structure(p)
+    sets = [set(v) for v, _, _ in cl]
+    parents = [par for _, par, _ in cl]
+    depths = [d for _, _, d in cl]
+    assert parents.count(-1) == 1
+    root = parents.index(-1)
+    assert root == info["root"]
+    # depth = BFS layer (Section 2's traversal): parent is one layer up
+    for c, par in enumerate(parents):
+        if par >= 0:
+            assert depths[c] == depths[par] + 1
+    assert info["n_levels"] == max(depths) + 1
+    # family coverage
+    for v in range(net.n):
+        fam = set(int(q) for q in net.parents_of(v)) | {v}
+        assert any(fam <= s for s in sets)
+    # running intersection
+    for x in range(net.n):
+        holders = [c for c, s in enumerate(sets) if x in s]
+        tops = [c for c in holders if parents[c] < 0 or x not in sets[parents[c]]]
+        assert len(tops) == 1
+    # layout: the upward separator is the outermost block, in the parent's order
+    for c, (vars_, par, _) in enumerate(cl):
+        if par < 0:
+            continue
+        sep = [v for v in cl[par][0] if v in sets[c]]
+        assert vars_[:len(sep)] == sep
+    # root rule
+    o = oracle.Oracle(net, root="largest" if root_rule == J.JT_ROOT_LARGEST else "center")
+    assert info["n_levels"] == o.height + 1
+    if root_rule == J.JT_ROOT_LARGEST:
+        sizes = [int(np.prod([net.card[v] for v in s])) for s in sets]
+        assert sizes[root] == max(sizes) and root == sizes.index(max(sizes))
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_tiny_networks_compile(seed):
+    net = tiny_random_network(seed)
+    cl, info = _structure(_plan(net))
+    o = oracle.Oracle(net)
+    assert sorted(tuple(sorted(v)) for v, _, _ in cl) == sorted(tuple(v) for v, _ in o.cliques())
+
+
+def test_validation_errors():
+    net = configs.network("bn20")
+    bad = make_network(net.n, net.card, [list(net.parents_of(v)) for v in range(net.n)], 1.0,
+                       np.random.default_rng(0))
+    bad.cpt = bad.cpt.copy()
+    bad.cpt[3] += 0.01  # a CPT row no longer sums to 1
+    with pytest.raises(J.JTError) as e:
+        _plan(bad)
+    assert e.value.status == J.JT_EINVAL
+    neg = make_network(net.n, net.card, [list(net.parents_of(v)) for v in range(net.n)], 1.0,
+                       np.random.default_rng(0))
+    neg.cpt = neg.cpt.copy()
+    neg.cpt[0], neg.cpt[1] = -0.5, 1.5
+    with pytest.raises(J.JTError) as e:
+        _plan(neg)
+    assert e.value.status == J.JT_EINVAL
+    # a directed cycle: 0 -> 1 -> 2 -> 0
+    cyc = make_network(3, [2, 2, 2], [[], [0], [1]], 1.0, np.random.default_rng(0))
+    cyc.parents = np.array([2, 0, 1], dtype=np.int32)
+    cyc.parent_ptr = np.array([0, 1, 2, 3], dtype=np.int32)
+    cyc.cpt = np.full(12, 0.5)
+    with pytest.raises(J.JTError) as e:
+        _plan(cyc)
+    assert e.value.status == J.JT_ECYCLE
+    # a clique above the configured limit
+    with pytest.raises(J.JTError) as e:
+        _plan(configs.network("bn60"), max_clique_entries=1000)
+    assert e.value.status == J.JT_ETOOBIG
+
+
+def test_algorithmic_bytes_formula():
+    net = configs.network("bn60")
+    info = _plan(net).info()
+    expect = (8 * info["sum_clique_entries"] + 16 * info["sum_sep_entries"] + 4 * net.n
+              + 8 * info["sum_card"] + 8)
+    assert info["algorithmic_bytes_per_case"] == expect
