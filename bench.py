@@ -111,6 +111,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_evidence_seed(name: str, rank: int) -> int:
+    """Each rank draws its own independent batch of the workload."""
+    from synth import configs
+    return configs.EVIDENCE_SEED[name] + 1000 * rank
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's timed region (all ranks get the same value)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(cases_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: the cases of all ranks over the slowest rank's time."""
+    return cases_per_rank * world / (ms_per_step / 1e3)
+
+
 def _oracle_rate(net, ev, threads, budget_s):
     """Oracle cases/s on up to len(ev) cases, stopping after ~budget_s."""
     import oracle  # CPU baseline leg only
@@ -179,8 +200,7 @@ def main():
     net = configs.network(name)
     n_cases = args.cases or DEFAULT_CASES[name]
     # every rank gets its own independent batch (weak scaling)
-    ev = configs.evidence(name, net, n_cases=n_cases,
-                          seed=configs.EVIDENCE_SEED[name] + 1000 * rank)
+    ev = configs.evidence(name, net, n_cases=n_cases, seed=rank_evidence_seed(name, rank))
 
     if args.impl == "reference":
         return run_reference(args, name, net, ev, rank, world)
@@ -225,13 +245,9 @@ def main():
     if dist:
         dist.barrier()
     clock_info = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_per_step = ms / args.steps
-    value = n_cases * world / (ms_per_step / 1e3)
+    value = aggregate_rate(n_cases, world, ms_per_step)
 
     # accuracy of the timed run's outputs on a seeded sample (oracle)
     lp = d_lp.cpu().numpy()

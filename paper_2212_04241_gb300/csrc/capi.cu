@@ -228,6 +228,7 @@ static jt_status upload_plan(jt_plan *pl) {
   const size_t o_cl = put(blob, P.dcl), o_map = put(blob, P.dmap), o_task = put(blob, P.dtask);
   const size_t o_ci = put(blob, P.citems), o_di = put(blob, P.ditems), o_ip = put(blob, P.ipool);
   const size_t o_b32 = put(blob, P.base32), o_card = put(blob, card32), o_po = put(blob, P.post_off);
+  const size_t o_cp = put(blob, P.comp_ptr), o_cv = put(blob, P.comp_vars), o_cc = put(blob, P.comp_cliques);
   JT_CUDA_TRY(cudaMalloc(&pl->d_static, blob.size()));
   pl->static_bytes = blob.size();
   JT_CUDA_TRY(cudaMemcpy(pl->d_static, blob.data(), blob.size(), cudaMemcpyHostToDevice));
@@ -242,10 +243,12 @@ static jt_status upload_plan(jt_plan *pl) {
   D.base32 = reinterpret_cast<const float *>(b + o_b32);
   D.card = reinterpret_cast<const int32_t *>(b + o_card);
   D.post_off = reinterpret_cast<const int64_t *>(b + o_po);
+  D.comp_ptr = reinterpret_cast<const int32_t *>(b + o_cp);
+  D.comp_vars = reinterpret_cast<const int32_t *>(b + o_cv);
+  D.comp_cliques = reinterpret_cast<const int32_t *>(b + o_cc);
   D.n_vars = P.n;
   D.n_cliques = (int32_t)P.cl.size();
   D.root = P.root;
-  D.base_exp_sum = P.base_exp_sum;
   D.psi_rows = P.sum_cl;
   D.sep_rows = P.sep_rows;
   D.post_rows = P.sum_card;

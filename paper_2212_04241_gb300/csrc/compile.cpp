@@ -644,6 +644,35 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   P.base_exp_sum = 0;
   for (int c = 0; c < m; ++c) P.base_exp_sum += base_exp[c];
 
+  // component trees: every variable belongs to exactly one (an empty
+  // separator shares no variable), listed under the component's root
+  {
+    std::vector<int> comp_root(m, -1);
+    for (int c : P.bfs) comp_root[c] = (c == root || P.cl[c].n_up == 0) ? c : comp_root[P.cl[c].parent];
+    std::vector<std::vector<int32_t>> members_of(m);
+    std::vector<char> seen(n, 0);
+    for (int c : P.bfs)
+      for (int v : P.cl[c].vars)
+        if (!seen[v]) { seen[v] = 1; members_of[comp_root[c]].push_back(v); }
+    P.comp_ptr.assign(m + 1, 0);
+    P.comp_vars.clear();
+    for (int c = 0; c < m; ++c) {
+      P.comp_vars.insert(P.comp_vars.end(), members_of[c].begin(), members_of[c].end());
+      P.comp_ptr[c + 1] = (int32_t)P.comp_vars.size();
+    }
+    std::vector<std::vector<int32_t>> cliques_of(m);
+    for (int c = 0; c < m; ++c) {
+      P.dcl[comp_root[c]].comp_base_exp += base_exp[c];
+      if (comp_root[c] != c) cliques_of[comp_root[c]].push_back(c);
+    }
+    P.comp_cliques.clear();
+    for (int c = 0; c < m; ++c) {
+      P.dcl[c].comp_begin = (int32_t)P.comp_cliques.size();
+      P.comp_cliques.insert(P.comp_cliques.end(), cliques_of[c].begin(), cliques_of[c].end());
+      P.dcl[c].comp_end = (int32_t)P.comp_cliques.size();
+    }
+  }
+
   // ---------------------------------------------------------------------
   // plain FP64 path maps: (var, card, src stride, dst stride) quadruples
   // ---------------------------------------------------------------------

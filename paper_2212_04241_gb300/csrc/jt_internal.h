@@ -27,6 +27,10 @@ struct DClique {
   int32_t parent;     // -1 for the root
   int32_t is_root;    // 1 for a component root: the tree root, or a clique
                       // whose separator towards its parent is empty
+  int32_t comp_begin; // component roots: the other cliques of the component,
+  int32_t comp_end;   //   [comp_begin, comp_end) in the comp_cliques list
+  int32_t comp_base_exp;  // component roots: sum of the component's base-table exponents
+  int32_t pad;
 };
 
 // A linear index map over a clique's entries: idx(s*R + u) = A[s] + B[u].
@@ -137,6 +141,10 @@ struct Plan {
   int64_t sep_rows = 0;           // rows of a tile's sep region (sum of nsep incl. root)
   int64_t n_groups = 0, n_partials = 0;
   int32_t base_exp_sum = 0;       // sum of the FP32 base-table power-of-two exponents
+  // variables of each component tree, listed under its root clique (CSR)
+  std::vector<int32_t> comp_ptr;  // [n_cliques + 1]
+  std::vector<int32_t> comp_vars; // [n]
+  std::vector<int32_t> comp_cliques;  // non-root cliques of each component, grouped by component
 
   // plain path
   std::vector<DPlainMap> pmap;

@@ -467,19 +467,26 @@ __global__ void k_finalize(DevPlan P, DevArena A, int W, int32_t n_cases, int64_
   if (wid >= n_cases) return;
   const int64_t tile = wid / W;
   const int c = (int)(wid % W);
-  // messages multiplied into a parent were scaled by 2^-k: add k back; every
-  // component root contributes the log of its total
+  // Messages multiplied into a parent were scaled by 2^-k: add k back.
+  // Every component root contributes the log of its total -- except a
+  // component without any observed variable, whose probability is exactly 1
+  // (a sum over all states of a product of CPTs) and contributes 0; its
+  // cliques' exponents are left out with it.
   long long K = 0;
   double lz = 0.0;
   int zero = 0;
   for (int cl = lane; cl < P.n_cliques; cl += 32) {
     const DClique &D = P.cl[cl];
-    if (D.is_root) {
-      const float z = A.phistar[(tile * P.sep_rows + D.sep_row) * W + c];
-      if (z > 0.f) lz += log((double)z); else zero = 1;
-    } else {
-      K += pow2_exp(A.maxbits[(tile * P.n_cliques + cl) * W + c]);
-    }
+    if (!D.is_root) continue;
+    bool observed = false;
+    for (int k = P.comp_ptr[cl]; k < P.comp_ptr[cl + 1] && !observed; ++k)
+      observed = A.ev[(tile * P.n_vars + P.comp_vars[k]) * W + c] >= 0;
+    if (!observed) continue;
+    const float z = A.phistar[(tile * P.sep_rows + D.sep_row) * W + c];
+    if (z > 0.f) lz += log((double)z); else zero = 1;
+    K += D.comp_base_exp;
+    for (int k = D.comp_begin; k < D.comp_end; ++k)
+      K += pow2_exp(A.maxbits[(tile * P.n_cliques + P.comp_cliques[k]) * W + c]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -493,7 +500,7 @@ __global__ void k_finalize(DevPlan P, DevArena A, int W, int32_t n_cases, int64_
   if (lane == 0) {
     double lp;
     if (st == JT_CASE_OK)
-      lp = lz + (double)(K + P.base_exp_sum) * 0.69314718055994530942;
+      lp = lz + (double)K * 0.69314718055994530942;
     else if (st == JT_CASE_ZERO_EVIDENCE)
       lp = -INFINITY;
     else

@@ -20,10 +20,13 @@ struct DevPlan {
   const float *base32;
   const int32_t *card;       // [n]
   const int64_t *post_off;   // [n]
+  const int32_t *comp_ptr;   // [n_cliques + 1] variables of the component rooted at a clique
+  const int32_t *comp_vars;  // [n]
+  const int32_t *comp_cliques;  // non-root cliques of each component
   int32_t n_vars;
   int32_t n_cliques;
   int32_t root;
-  int32_t base_exp_sum;      // sum over cliques of the base-table exponents
+  int32_t pad0;
   int64_t psi_rows;          // rows of one tile's psi region (sum |C|)
   int64_t sep_rows;          // rows of one tile's message regions
   int64_t post_rows;         // rows of one tile's posterior region (sum card)
