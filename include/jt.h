@@ -162,6 +162,34 @@ JT_API jt_status jt_infer_device(jt_plan *plan, int32_t n_cases, const int32_t *
                           void *cuda_stream);
 
 /*
+ * Size of the fixed device array behind jt_infer_device_noalloc (64 MiB).
+ */
+#define JT_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * The paper has no counterpart to this call; it is a deployment variant of
+ * jt_infer_device for callers that cannot allocate device memory while
+ * serving -- a process whose device memory is owned by another allocator,
+ * a latency-bound loop that cannot afford cudaMalloc/cudaFree (they
+ * synchronise the whole device), or a deployment that forbids allocation
+ * after start-up.  Same arguments, results and stream semantics as
+ * jt_infer_device; it allocates nothing: the per-batch tables live in one
+ * fixed device array of JT_NOALLOC_SCRATCH_BYTES that the library defines
+ * (every GPU that loads the library keeps it until the process exits).
+ * The first call on a device looks up that array's device address, so make
+ * the first call before any stream capture.  All calls, for every plan,
+ * share the one array and leave their contents in it; calls whose work
+ * overlaps on the GPU (different streams, threads or plans at once) race
+ * and give wrong results -- serialise them.  A plan whose tables for one
+ * case tile (jt_plan_info: tile_cases cases) exceed the array is refused
+ * with JT_ENOMEM and a message from jt_last_error; larger batches are run
+ * in chunks that fit.
+ */
+JT_API jt_status jt_infer_device_noalloc(jt_plan *plan, int32_t n_cases, const int32_t *d_evidence,
+                                         double *d_log_pe, double *d_posteriors,
+                                         int32_t *d_case_status, void *cuda_stream);
+
+/*
  * The plain per-case FP64 GPU path (measurement comparator, element-wise
  * style of the prior GPU approach the paper compares against, Section 1 and
  * Section 3 "Elem."): the same plan, FP64 tables, one case at a time, one

@@ -18,7 +18,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libjt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_UNITS = ["kernels.cu", "capi.cu", "serve.cu"]
+CUDA_UNITS = ["kernels.cu", "capi.cu", "serve.cu", "noalloc.cu"]
 CXX_UNITS = ["compile.cpp"]
 
 
