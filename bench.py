@@ -181,7 +181,8 @@ def run_reference(args, name, net, ev, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps; default: as many as fill about 2 s")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bn60", choices=sorted(WORKLOADS))
@@ -229,9 +230,16 @@ def main():
         step()
     torch.cuda.synchronize()
     info = plan.info()
+    if args.steps <= 0:
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        one = max(time.perf_counter() - t0, 1e-5)
+        args.steps = int(min(5000, max(10, 2.0 / one)))
 
     clocks = ClockSampler(local_rank)
     clocks.start()
+    time.sleep(0.5)  # let the sampler start before the timed region
     if dist:
         dist.barrier()
     torch.cuda.synchronize()

@@ -71,6 +71,8 @@ static void arena_bind(const Plan &P, Arena &a, char *mem, int tiles) {
   a.da.counters = reinterpret_cast<uint32_t *>(take(L.counters));
   a.da.ev = reinterpret_cast<int32_t *>(take(L.ev));
   a.da.bad = reinterpret_cast<int32_t *>(take(L.bad));
+  a.da.errflag = reinterpret_cast<uint32_t *>(mem + off);
+  off += ArenaLayout::kTail;
   a.da.tiles = tiles;
   a.mem = mem;
   a.bytes = off;
@@ -81,7 +83,7 @@ jt_status arena_alloc(const Plan &P, Arena &a, int tiles) {
   arena_free(a);
   const ArenaLayout L = arena_layout(P);
   void *mem = nullptr;
-  cudaError_t e = cudaMalloc(&mem, L.per_tile * (size_t)tiles);
+  cudaError_t e = cudaMalloc(&mem, L.bytes(tiles));
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error(std::string("arena cudaMalloc: ") + cudaGetErrorString(e));
@@ -89,15 +91,16 @@ jt_status arena_alloc(const Plan &P, Arena &a, int tiles) {
   }
   a.owns = true;
   arena_bind(P, a, static_cast<char *>(mem), tiles);
-  // counters start at zero; every combining block resets its own counter
+  // counters start at zero; every combining warp resets its own counter
   JT_CUDA_TRY(cudaMemset(a.da.counters, 0, L.counters * (size_t)tiles));
+  JT_CUDA_TRY(cudaMemset(a.da.errflag, 0, sizeof(uint32_t)));
   return JT_OK;
 }
 
 jt_status arena_wrap(const Plan &P, Arena &a, void *mem, size_t bytes, int tiles) {
   arena_free(a);
   const ArenaLayout L = arena_layout(P);
-  if (L.per_tile * (size_t)tiles > bytes) {
+  if (L.bytes(tiles) > bytes) {
     set_error("arena buffer too small");
     return JT_ENOMEM;
   }
@@ -171,6 +174,17 @@ jt_status run_chunk(jt_plan *pl, Arena &a, const int32_t *d_ev, int32_t nc, doub
   return JT_OK;
 }
 
+jt_status check_arena_flag(Arena &a) {
+  uint32_t f = 0;
+  JT_CUDA_TRY(cudaMemcpy(&f, a.da.errflag, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f) {
+    cudaMemset(a.da.errflag, 0, sizeof(uint32_t));
+    set_error("a bounded device wait expired (TMA copy not completed)");
+    return JT_ETIMEOUT;
+  }
+  return JT_OK;
+}
+
 int budget_tiles(const jt_plan *pl, int64_t budget_bytes) {
   const ArenaLayout L = arena_layout(pl->P);
   if (budget_bytes <= 0) {
@@ -178,7 +192,8 @@ int budget_tiles(const jt_plan *pl, int64_t budget_bytes) {
     cudaMemGetInfo(&fr, &tot);
     budget_bytes = std::min<int64_t>(96LL << 30, (int64_t)(0.6 * (double)fr));
   }
-  return (int)std::min<int64_t>(budget_bytes / (int64_t)L.per_tile, kMaxTilesPerChunk);
+  return (int)std::min<int64_t>((budget_bytes - (int64_t)ArenaLayout::kTail) / (int64_t)L.per_tile,
+                                kMaxTilesPerChunk);
 }
 
 // Make the plan's default arena hold at least min(need, budget) tiles.
@@ -229,6 +244,7 @@ static jt_status upload_plan(jt_plan *pl) {
   const size_t o_ci = put(blob, P.citems), o_di = put(blob, P.ditems), o_ip = put(blob, P.ipool);
   const size_t o_b32 = put(blob, P.base32), o_card = put(blob, card32), o_po = put(blob, P.post_off);
   const size_t o_cp = put(blob, P.comp_ptr), o_cv = put(blob, P.comp_vars), o_cc = put(blob, P.comp_cliques);
+  const size_t o_cr = put(blob, P.comp_roots), o_pg = put(blob, P.pgroup_ptr);
   JT_CUDA_TRY(cudaMalloc(&pl->d_static, blob.size()));
   pl->static_bytes = blob.size();
   JT_CUDA_TRY(cudaMemcpy(pl->d_static, blob.data(), blob.size(), cudaMemcpyHostToDevice));
@@ -246,6 +262,10 @@ static jt_status upload_plan(jt_plan *pl) {
   D.comp_ptr = reinterpret_cast<const int32_t *>(b + o_cp);
   D.comp_vars = reinterpret_cast<const int32_t *>(b + o_cv);
   D.comp_cliques = reinterpret_cast<const int32_t *>(b + o_cc);
+  D.comp_roots = reinterpret_cast<const int32_t *>(b + o_cr);
+  D.n_comp = (int32_t)P.comp_roots.size();
+  D.pgroup_ptr = reinterpret_cast<const int32_t *>(b + o_pg);
+  D.n_pgroups = (int32_t)P.pgroup_ptr.size() - 1;
   D.n_vars = P.n;
   D.n_cliques = (int32_t)P.cl.size();
   D.root = P.root;
@@ -257,11 +277,12 @@ static jt_status upload_plan(jt_plan *pl) {
   int max_maps = 0;
   for (const Level &lv : P.levels) max_maps = std::max(max_maps, lv.c_max_maps);
   const size_t smem = collect_smem_bytes(P.cpt_per_thread, max_maps);
-  if (smem > 227 * 1024) {
-    set_error("a clique has too many child messages and evidence variables for one thread block");
+  if (collect_warp_smem_bytes(P.cpt_per_thread, max_maps) > kCollectSmemLimit) {
+    set_error("a clique has too many child messages and evidence variables for one warp's shared memory");
     return JT_ETOOBIG;
   }
   JT_CUDA_TRY(configure_collect_smem(P.cpt_per_thread, smem));
+  JT_CUDA_TRY(configure_distribute_smem(P.cpt_per_thread));
   return JT_OK;
 }
 
@@ -352,7 +373,7 @@ extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
   o->distribute_items = (int64_t)P.ditems.size();
   o->algorithmic_bytes_per_case = 8.0 * (double)P.sum_cl + 16.0 * (double)P.sum_sep + 4.0 * P.n +
                                   8.0 * (double)P.sum_card + 8.0;
-  int k = 2;  // evidence + finalize
+  int k = 3;  // evidence + log P(e) + posteriors
   for (const Level &lv : P.levels) {
     k += lv.c_item_end > lv.c_item_begin;
     k += lv.d_item_end > lv.d_item_begin;
@@ -465,6 +486,8 @@ extern "C" jt_status jt_infer(jt_plan *pl, int32_t n_cases, const int32_t *ev, d
     JT_CUDA_TRY(cudaMemcpyAsync(h_po, d_po, sizeof(double) * (size_t)nc * P.sum_card, cudaMemcpyDeviceToHost, s));
     JT_CUDA_TRY(cudaMemcpyAsync(h_st, d_st, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, s));
     JT_CUDA_TRY(cudaStreamSynchronize(s));
+    st = check_arena_flag(pl->arena);
+    if (st != JT_OK) return st;
     std::memcpy(lp + b, h_lp, sizeof(double) * nc);
     std::memcpy(post + b * P.sum_card, h_po, sizeof(double) * (size_t)nc * P.sum_card);
     std::memcpy(cst + b, h_st, sizeof(int32_t) * nc);
@@ -663,6 +686,8 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
   const int stop = mark();
   JT_CUDA_TRY(cudaGetLastError());
   JT_CUDA_TRY(cudaStreamSynchronize(s));
+  st = check_arena_flag(pl->arena);
+  if (st != JT_OK) return st;
   for (int k = 0; k < 6; ++k) out[k] = 0;
   for (const Span &sp : spans) {
     float ms = 0;

@@ -386,7 +386,25 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     }
     if (P.assign[v] < 0) { err = "internal: no clique covers a family"; return JT_EINVAL; }
     P.cl[P.assign[v]].homed.push_back(v);
-    P.cl[P.post_src[v]].owned.push_back(v);
+  }
+  // Posterior source of each variable in the batched path: the smallest
+  // table holding it -- a separator (its calibrated marginal is phi* x rho)
+  // when one is no larger than the smallest clique, else that clique.
+  for (int v = 0; v < n; ++v) {
+    int best_sep = -1;
+    double best_sep_size = 0;
+    for (int c = 0; c < m; ++c) {
+      const HostClique &C = P.cl[c];
+      if (C.parent < 0 || C.n_up == 0) continue;
+      if (std::find(C.vars.begin(), C.vars.begin() + C.n_up, v) == C.vars.begin() + C.n_up) continue;
+      double sz = 1;
+      for (int i = 0; i < C.n_up; ++i) sz *= C.card[i];
+      if (best_sep < 0 || sz < best_sep_size) { best_sep = c; best_sep_size = sz; }
+    }
+    if (best_sep >= 0 && best_sep_size <= csize[P.post_src[v]])
+      P.cl[best_sep].owned_sep.push_back(v);
+    else
+      P.cl[P.post_src[v]].owned.push_back(v);
   }
 
   P.sum_cl = P.max_cl = P.sum_sep = 0;
@@ -519,23 +537,27 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   std::vector<std::vector<int>> tasks_of(m);
   for (int c = 0; c < m; ++c) {
     const HostClique &C = P.cl[c];
-    auto make_task = [&](const std::vector<int> &target, int kind, int dst, int64_t dst_row) {
-      // target variables in C's layout order
+    auto make_task = [&](const std::vector<int> &target, int kind, int dst, int64_t dst_row, bool from_sep = false) {
+      // target variables in the source table's layout order (the clique, or
+      // its upward separator = the first n_up variables)
+      const int nv = from_sep ? C.n_up : (int)C.vars.size();
       std::vector<int> tpos, upos;
-      for (int i = 0; i < (int)C.vars.size(); ++i) {
+      for (int i = 0; i < nv; ++i) {
         bool in = std::find(target.begin(), target.end(), C.vars[i]) != target.end();
         (in ? tpos : upos).push_back(i);
       }
       std::vector<int> tcard, ucard;
       std::vector<int64_t> wa, wsa, wb, wsb;
+      // stride inside the source table / inside the upward separator
+      auto xs = [&](int i) { return from_sep ? C.stride[i] / C.R : C.stride[i]; };
       for (int i : tpos) {
         tcard.push_back(C.card[i]);
-        wa.push_back(C.stride[i]);
+        wa.push_back(xs(i));
         wsa.push_back(i < C.n_up ? C.stride[i] / C.R : 0);
       }
       for (int i : upos) {
         ucard.push_back(C.card[i]);
-        wb.push_back(C.stride[i]);
+        wb.push_back(xs(i));
         wsb.push_back(i < C.n_up ? C.stride[i] / C.R : 0);
       }
       DTask t{};
@@ -551,6 +573,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       t.kind = kind;
       t.dst = dst;
       t.dst_row = dst_row;
+      t.src_sep = from_sep ? 1 : 0;
       tasks_of[c].push_back((int)P.dtask.size());
       P.dtask.push_back(t);
     };
@@ -561,26 +584,39 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       make_task(sv, TASK_CHILD, ch, sep_row[ch]);
     }
     for (int v : C.owned) make_task(std::vector<int>{v}, TASK_POSTERIOR, v, P.post_off[v]);
+    for (int v : C.owned_sep) make_task(std::vector<int>{v}, TASK_POSTERIOR, v, P.post_off[v], true);
   }
 
   // ---------------------------------------------------------------------
   // per-layer thread-block lists
   // ---------------------------------------------------------------------
   const int NW = 8;  // warps per block
-  P.cpt_per_thread = opts.cases_per_thread > 0 ? opts.cases_per_thread : 4;
-  if (P.cpt_per_thread != 1 && P.cpt_per_thread != 2 && P.cpt_per_thread != 4) {
-    err = "cases_per_thread must be 1, 2 or 4";
+  P.cpt_per_thread = opts.cases_per_thread > 0 ? opts.cases_per_thread : 8;
+  if (P.cpt_per_thread != 1 && P.cpt_per_thread != 2 && P.cpt_per_thread != 4 && P.cpt_per_thread != 8) {
+    err = "cases_per_thread must be 1, 2, 4 or 8";
     return JT_EINVAL;
   }
   P.tile = 32 * P.cpt_per_thread;
-  P.rows_per_cta = opts.rows_per_cta > 0 ? opts.rows_per_cta : (P.cpt_per_thread == 4 ? 512 : 1024);
-  const int64_t ROWS = P.rows_per_cta;
+  // Rows per warp item: fixed by the option (rows per block / warps), else
+  // chosen per layer so that a layer has about 192 warp items per case tile,
+  // between 32 rows (one index batch) and 512: a small layer is
+  // latency-bound and finishes sooner in short items, a big one amortises
+  // each item's set-up over long ones.
+  P.rows_per_cta = opts.rows_per_cta > 0 ? opts.rows_per_cta : 0;
+  auto layer_rows = [&](int64_t total) -> int64_t {
+    if (opts.rows_per_cta > 0) return std::max<int64_t>(1, opts.rows_per_cta / NW);
+    int64_t r = 32;
+    while (r < 512 && r * 2 * 192 <= total) r *= 2;
+    return r;
+  };
   P.citems.clear();
   P.ditems.clear();
   P.n_groups = 0;
   P.n_partials = 0;
-  auto emit = [&](std::vector<DItem> &out, int task, int64_t nseg, int64_t rows) {
-    if (rows <= ROWS / NW) {
+  // one item per warp: whole segments when a segment fits the warp's rows,
+  // else the segment is split into pieces combined in piece order
+  auto emit = [&](std::vector<DItem> &out, int task, int64_t nseg, int64_t rows, int64_t ROWS) {
+    if (rows <= ROWS) {
       int64_t per = std::max<int64_t>(1, ROWS / rows);
       for (int64_t t0 = 0; t0 < nseg; t0 += per) {
         DItem it{};
@@ -628,21 +664,39 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   for (int L = 0; L <= P.height; ++L) {
     Level &lv = P.levels[L];
     lv.c_item_begin = (int64_t)P.citems.size();
+    int64_t crows = 0, drows = 0;
     for (int c = 0; c < m; ++c) {
       if (P.cl[c].depth != L) continue;
-      emit(P.citems, c, P.cl[c].nsep, P.cl[c].R);
+      crows += P.cl[c].size;
+      for (int t : tasks_of[c]) drows += P.dtask[t].T * P.dtask[t].U;
+    }
+    const int64_t cR = layer_rows(crows), dR = layer_rows(drows);
+    for (int c = 0; c < m; ++c) {
+      if (P.cl[c].depth != L) continue;
+      emit(P.citems, c, P.cl[c].nsep, P.cl[c].R, cR);
       lv.c_max_maps = std::max(lv.c_max_maps, P.dcl[c].map_end - P.dcl[c].map_begin);
     }
     lv.c_item_end = (int64_t)P.citems.size();
     lv.d_item_begin = (int64_t)P.ditems.size();
     for (int c = 0; c < m; ++c) {
       if (P.cl[c].depth != L) continue;
-      for (int t : tasks_of[c]) emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U);
+      for (int t : tasks_of[c]) emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U, dR);
     }
     lv.d_item_end = (int64_t)P.ditems.size();
   }
   P.base_exp_sum = 0;
   for (int c = 0; c < m; ++c) P.base_exp_sum += base_exp[c];
+
+  // variable groups of the posterior kernel (a block per tile and group)
+  P.pgroup_ptr.assign(1, 0);
+  {
+    int cols = 0;
+    for (int v = 0; v < n; ++v) {
+      if (cols > 0 && cols + card[v] > 16) { P.pgroup_ptr.push_back(v); cols = 0; }
+      cols += card[v];
+    }
+    P.pgroup_ptr.push_back(n);
+  }
 
   // component trees: every variable belongs to exactly one (an empty
   // separator shares no variable), listed under the component's root
@@ -666,6 +720,9 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       if (comp_root[c] != c) cliques_of[comp_root[c]].push_back(c);
     }
     P.comp_cliques.clear();
+    P.comp_roots.clear();
+    for (int c = 0; c < m; ++c)
+      if (comp_root[c] == c) P.comp_roots.push_back(c);
     for (int c = 0; c < m; ++c) {
       P.dcl[c].comp_begin = (int32_t)P.comp_cliques.size();
       P.comp_cliques.insert(P.comp_cliques.end(), cliques_of[c].begin(), cliques_of[c].end());

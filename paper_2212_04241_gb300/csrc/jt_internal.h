@@ -45,9 +45,12 @@ struct DMap {
   int32_t src;        // child clique / variable
 };
 
-// A distribute target of a clique: for t in [0, T),
-//   value(t) = sum_{u < U} psi[A[t] + B[u]] * rho[sA[t] + sB[u]]
-// where rho is the clique's own upward ratio (a component root uses 2^-k).
+// A distribute target: for t in [0, T),
+//   value(t) = sum_{u < U} X[A[t] + B[u]] * Y[sA[t] + sB[u]]
+// src_sep == 0: X = psi of `clique`, Y = its upward ratio rho (a component
+//   root uses 2^-k instead);
+// src_sep == 1: X = phi* and Y = rho of the separator above `clique` (their
+//   product is that separator's calibrated marginal; sA = A, sB = B).
 //   kind TASK_CHILD: writes rho_child[t] = value(t) / phistar_child[t]
 //   kind TASK_POSTERIOR: writes the unnormalised marginal of variable dst
 enum { TASK_CHILD = 0, TASK_POSTERIOR = 1 };
@@ -58,7 +61,7 @@ struct DTask {
   int32_t clique;     // source clique
   int32_t kind;
   int32_t dst;        // child clique / variable
-  int32_t pad;
+  int32_t src_sep;
 };
 
 // One thread block of a layer launch (the same list serves every tile).
@@ -100,7 +103,8 @@ struct HostClique {
   int parent = -1, depth = 0;
   std::vector<int> children;
   std::vector<int> homed;       // variables whose evidence this clique applies
-  std::vector<int> owned;       // variables whose posterior this clique provides
+  std::vector<int> owned;       // variables whose posterior this clique's table provides
+  std::vector<int> owned_sep;   // variables whose posterior its upward separator provides
 };
 
 struct Level {
@@ -126,7 +130,7 @@ struct Plan {
   int height = 0;
   std::vector<int> bfs;           // BFS order from the root
   std::vector<int> assign;        // CPT v -> clique
-  std::vector<int> post_src;      // variable -> clique that owns its posterior
+  std::vector<int> post_src;      // variable -> smallest clique containing it
   int64_t sum_cl = 0, max_cl = 0, sum_sep = 0;
 
   // device-side description (host copies)
@@ -145,6 +149,8 @@ struct Plan {
   std::vector<int32_t> comp_ptr;  // [n_cliques + 1]
   std::vector<int32_t> comp_vars; // [n]
   std::vector<int32_t> comp_cliques;  // non-root cliques of each component, grouped by component
+  std::vector<int32_t> comp_roots;    // component root cliques
+  std::vector<int32_t> pgroup_ptr;    // consecutive variable groups of <= 16 posterior columns
 
   // plain path
   std::vector<DPlainMap> pmap;

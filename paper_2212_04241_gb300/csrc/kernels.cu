@@ -5,9 +5,11 @@
 // that layer (Section 2: BFS layers, all table entries of a layer packed
 // into one parallel task) for every evidence case of the chunk: the grid is
 // (thread blocks of the layer's work list) x (case tiles).  Tables are
-// [tile][row][W] with W = 32 * CPT consecutive cases per row, so every index
-// computation is uniform across a warp and amortised over W cases, and every
-// row access is a fully coalesced W*4-byte transaction.
+// [tile][row][W] with W = 32 * CPT consecutive evidence cases per row; a
+// warp owns a contiguous range of rows of one table and moves one whole row
+// (W * 4 bytes, fully coalesced) per access, so every index computation is
+// shared by the W cases of a row.  Row indices are computed 32 rows at a
+// time, one row per lane, and broadcast; rows are loaded four at a time.
 //
 //   collect (Section 2: reduction + extension + marginalisation, fused):
 //     psi_C[e] = base_C[e] * [evidence of homed variables] *
@@ -30,10 +32,23 @@
 namespace jt {
 namespace {
 
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGroup = 4;  // rows whose loads a warp issues together
+
+// CPT cases of one thread inside a row of W = 32*CPT cases.  For CPT >= 4
+// the thread holds CPT/4 float4 pieces, piece v at columns 128*v + 4*lane;
+// for CPT < 4 one piece at columns CPT*lane.  Every access of a warp to a
+// row is a contiguous 512-byte (or 128/256-byte) transaction per piece.
 template <int CPT>
 struct Vec {
   float x[CPT];
 };
+
+template <int CPT>
+__device__ __forceinline__ int col_of(int lane, int k) {
+  if constexpr (CPT >= 4) return 128 * (k >> 2) + 4 * lane + (k & 3);
+  else return CPT * lane + k;
+}
 
 template <int CPT>
 __device__ __forceinline__ Vec<CPT> vzero() {
@@ -44,84 +59,71 @@ __device__ __forceinline__ Vec<CPT> vzero() {
 }
 
 template <int CPT>
-__device__ __forceinline__ Vec<CPT> ld_plain(const float *p) {
+__device__ __forceinline__ Vec<CPT> vsplat(float a) {
   Vec<CPT> r;
-  if constexpr (CPT == 4) {
-    float4 t = *reinterpret_cast<const float4 *>(p);
-    r.x[0] = t.x; r.x[1] = t.y; r.x[2] = t.z; r.x[3] = t.w;
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) r.x[k] = a;
+  return r;
+}
+
+enum LoadMode { LD_PLAIN, LD_STREAM, LD_NC, LD_CG };
+
+template <LoadMode M, class T>
+__device__ __forceinline__ T ld1(const T *p) {
+  if constexpr (M == LD_STREAM) return __ldcs(p);
+  else if constexpr (M == LD_NC) return __ldg(p);
+  else if constexpr (M == LD_CG) return __ldcg(p);
+  else return *p;
+}
+
+// Load this thread's CPT cases of the row starting at `row`.
+template <int CPT, LoadMode M = LD_PLAIN>
+__device__ __forceinline__ Vec<CPT> ldrow(const float *row, int lane) {
+  Vec<CPT> r;
+  if constexpr (CPT >= 4) {
+#pragma unroll
+    for (int v = 0; v < CPT / 4; ++v) {
+      const float4 t = ld1<M>(reinterpret_cast<const float4 *>(row + 128 * v + 4 * lane));
+      r.x[4 * v] = t.x; r.x[4 * v + 1] = t.y; r.x[4 * v + 2] = t.z; r.x[4 * v + 3] = t.w;
+    }
   } else if constexpr (CPT == 2) {
-    float2 t = *reinterpret_cast<const float2 *>(p);
+    const float2 t = ld1<M>(reinterpret_cast<const float2 *>(row + 2 * lane));
     r.x[0] = t.x; r.x[1] = t.y;
   } else {
-    r.x[0] = *p;
+    r.x[0] = ld1<M>(row + lane);
   }
   return r;
 }
 
-// read-once data (streamed from HBM)
-template <int CPT>
-__device__ __forceinline__ Vec<CPT> ld_stream(const float *p) {
-  Vec<CPT> r;
-  if constexpr (CPT == 4) {
-    float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
-    r.x[0] = t.x; r.x[1] = t.y; r.x[2] = t.z; r.x[3] = t.w;
+template <int CPT, bool STREAM = false>
+__device__ __forceinline__ void strow(float *row, int lane, const Vec<CPT> &a) {
+  if constexpr (CPT >= 4) {
+#pragma unroll
+    for (int v = 0; v < CPT / 4; ++v) {
+      float4 *p = reinterpret_cast<float4 *>(row + 128 * v + 4 * lane);
+      const float4 t = make_float4(a.x[4 * v], a.x[4 * v + 1], a.x[4 * v + 2], a.x[4 * v + 3]);
+      if constexpr (STREAM) __stcs(p, t); else *p = t;
+    }
   } else if constexpr (CPT == 2) {
-    float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
-    r.x[0] = t.x; r.x[1] = t.y;
+    float2 *p = reinterpret_cast<float2 *>(row + 2 * lane);
+    const float2 t = make_float2(a.x[0], a.x[1]);
+    if constexpr (STREAM) __stcs(p, t); else *p = t;
   } else {
-    r.x[0] = __ldcs(p);
-  }
-  return r;
-}
-
-// data written by other blocks of the same launch: bypass L1
-template <int CPT>
-__device__ __forceinline__ Vec<CPT> ld_cg(const float *p) {
-  Vec<CPT> r;
-  if constexpr (CPT == 4) {
-    float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
-    r.x[0] = t.x; r.x[1] = t.y; r.x[2] = t.z; r.x[3] = t.w;
-  } else if constexpr (CPT == 2) {
-    float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
-    r.x[0] = t.x; r.x[1] = t.y;
-  } else {
-    r.x[0] = __ldcg(p);
-  }
-  return r;
-}
-
-template <int CPT>
-__device__ __forceinline__ void st_plain(float *p, const Vec<CPT> &v) {
-  if constexpr (CPT == 4) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v.x[0], v.x[1], v.x[2], v.x[3]);
-  } else if constexpr (CPT == 2) {
-    *reinterpret_cast<float2 *>(p) = make_float2(v.x[0], v.x[1]);
-  } else {
-    *p = v.x[0];
+    if constexpr (STREAM) __stcs(row + lane, a.x[0]); else row[lane] = a.x[0];
   }
 }
 
-// write-once data that is read back only much later
+// Compensated (Kahan) accumulation per case of a partial sum: long FP32
+// sums keep a few ulp.
 template <int CPT>
-__device__ __forceinline__ void st_stream(float *p, const Vec<CPT> &v) {
-  if constexpr (CPT == 4) {
-    __stcs(reinterpret_cast<float4 *>(p), make_float4(v.x[0], v.x[1], v.x[2], v.x[3]));
-  } else if constexpr (CPT == 2) {
-    __stcs(reinterpret_cast<float2 *>(p), make_float2(v.x[0], v.x[1]));
-  } else {
-    __stcs(p, v.x[0]);
-  }
-}
-
-// Compensated (Kahan) accumulation per case: long FP32 sums keep ~2 ulp.
-template <int CPT>
-__device__ __forceinline__ void kahan_add(Vec<CPT> &sum, Vec<CPT> &comp, const Vec<CPT> &v) {
+__device__ __forceinline__ void kahan_fold(Vec<CPT> &sum, Vec<CPT> &comp, Vec<CPT> &part) {
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
-    float y = v.x[k] - comp.x[k];
-    float t = sum.x[k] + y;
+    const float y = part.x[k] - comp.x[k];
+    const float t = sum.x[k] + y;
     comp.x[k] = (t - sum.x[k]) - y;
     sum.x[k] = t;
+    part.x[k] = 0.f;
   }
 }
 
@@ -161,369 +163,374 @@ __global__ void k_evidence(const int32_t *__restrict__ ev_in, int32_t n_cases, D
 }
 
 // ---------------------------------------------------------------------------
+// shared pieces of the layer kernels
+// ---------------------------------------------------------------------------
+//
+// The unit of work is one warp: an item (DItem) gives a warp whole segments
+// of one table, or a row range of one segment ("split" item).  A block holds
+// kWarps independent items -- possibly of different cliques -- and never
+// synchronises, so small cliques pack together and no warp waits for another.
+
+// Rows of a warp's item: non-split items own whole segments [t0, t0+nt) of
+// R rows each (flattened in segment order); split items own rows
+// [u0, u0+nu) of segment t0.
+__device__ __forceinline__ void item_rows(const DItem &it, int32_t R, int32_t &s_first, int32_t &u_first,
+                                          int32_t &count) {
+  s_first = (int32_t)it.t0;
+  if (!it.split) {
+    u_first = 0;
+    count = (int32_t)(it.nt * (int64_t)R);
+  } else {
+    u_first = (int32_t)it.u0;
+    count = (int32_t)it.nu;
+  }
+}
+
+// Combine the partial sums of a split segment: every piece (one warp) writes
+// its sum, and the last piece to finish adds all of them in piece order.
+// Returns true in the warp that holds the final value, with `tot` set.
+template <int CPT>
+__device__ __forceinline__ bool combine_split(const DItem &it, const DevPlan &P, const DevArena &A, int tile,
+                                              int lane, const Vec<CPT> &acc, Vec<CPT> &tot) {
+  constexpr int W = 32 * CPT;
+  if (it.npieces == 1) {
+    tot = acc;
+    return true;
+  }
+  strow<CPT>(A.partial + ((int64_t)tile * P.n_partials + it.partial) * W, lane, acc);
+  __threadfence();
+  __syncwarp();
+  unsigned old = 0;
+  if (lane == 0) old = atomicAdd(&A.counters[(int64_t)tile * P.n_groups + it.group], 1u);
+  old = __shfl_sync(kFull, old, 0);
+  if (old != (unsigned)(it.npieces - 1)) return false;
+  __threadfence();
+  const int first = it.partial - it.piece;
+  tot = vzero<CPT>();
+  for (int p = 0; p < it.npieces; ++p) {
+    const Vec<CPT> x = ldrow<CPT, LD_CG>(A.partial + ((int64_t)tile * P.n_partials + first + p) * W, lane);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) tot.x[k] += x.x[k];
+  }
+  if (lane == 0) A.counters[(int64_t)tile * P.n_groups + it.group] = 0u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // collect
 // ---------------------------------------------------------------------------
-struct CollectSmem {
-  int64_t *mA, *mB, *mrow;
-  float *mval, *red, *redm;
-  int32_t *segA;
-};
 
-__host__ __device__ inline size_t collect_smem_layout(int cpt, int nm, CollectSmem *s, unsigned char *base) {
+// Shared memory of one warp: per map its per-case scale or evidence (read
+// as float4, so it comes first and every part is rounded to 16 bytes), its
+// index-table offsets and message row, and the map indices of 32 rows.
+__host__ __device__ inline size_t round16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline size_t collect_warp_smem(int cpt, int nm) {
   const int W = 32 * cpt;
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    size_t o = off;
-    off += (bytes + 15) & ~size_t(15);
-    return o;
-  };
-  size_t oA = take(sizeof(int64_t) * nm), oB = take(sizeof(int64_t) * nm), oR = take(sizeof(int64_t) * nm);
-  size_t oV = take(sizeof(float) * nm * W), oS = take(sizeof(float) * kWarps * W),
-         oM = take(sizeof(float) * kWarps * W), oG = take(sizeof(int32_t) * kWarps * nm);
-  if (s) {
-    s->mA = reinterpret_cast<int64_t *>(base + oA);
-    s->mB = reinterpret_cast<int64_t *>(base + oB);
-    s->mrow = reinterpret_cast<int64_t *>(base + oR);
-    s->mval = reinterpret_cast<float *>(base + oV);
-    s->red = reinterpret_cast<float *>(base + oS);
-    s->redm = reinterpret_cast<float *>(base + oM);
-    s->segA = reinterpret_cast<int32_t *>(base + oG);
-  }
-  return off;
+  return round16(sizeof(float) * W * (size_t)nm) + round16(3 * sizeof(int64_t) * (size_t)nm) +
+         round16(sizeof(int32_t) * 32 * (size_t)nm);
 }
 
 template <int CPT>
-__global__ void __launch_bounds__(kThreads) k_collect(DevPlan P, DevArena A, int64_t item_begin) {
+__global__ void __launch_bounds__(kThreads, 2) k_collect(DevPlan P, DevArena A, int64_t item_begin,
+                                                          int64_t n_items, int max_maps) {
   constexpr int W = 32 * CPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_nchild;
-  __shared__ int s_last;
-  const DItem it = P.citems[item_begin + blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (iw >= n_items) return;
+  const DItem it = P.citems[item_begin + iw];
   const int tile = blockIdx.y;
   const DClique C = P.cl[it.task];
   const int nm = C.map_end - C.map_begin;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  CollectSmem S;
-  collect_smem_layout(CPT, nm, &S, smem_raw);
+  unsigned char *ws = smem_raw + (size_t)warp * collect_warp_smem(CPT, max_maps);  // 16-byte aligned
+  float *mval = reinterpret_cast<float *>(ws);
+  int64_t *mA = reinterpret_cast<int64_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps));
+  int64_t *mB = mA + max_maps;
+  int64_t *mrow = mB + max_maps;
+  int32_t *idx = reinterpret_cast<int32_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps) +
+                                             round16(3 * sizeof(int64_t) * (size_t)max_maps));
 
-  for (int i = threadIdx.x; i < nm; i += kThreads) {
+  int nchild = 0;
+  for (int i = 0; i < nm; ++i) {
     const DMap mp = P.maps[C.map_begin + i];
-    S.mA[i] = mp.A_off;
-    S.mB[i] = mp.B_off;
-    S.mrow[i] = ((int64_t)tile * P.sep_rows + mp.src_row) * W;
+    if (lane == 0) {
+      mA[i] = mp.A_off;
+      mB[i] = mp.B_off;
+      mrow[i] = ((int64_t)tile * P.sep_rows + mp.src_row) * W;
+    }
+    nchild += (mp.kind == MAP_CHILD);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int c = col_of<CPT>(lane, k);
+      mval[i * W + c] = (mp.kind == MAP_CHILD)
+                            ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]))
+                            : __int_as_float(A.ev[((int64_t)tile * P.n_vars + mp.src) * W + c]);
+    }
   }
-  if (threadIdx.x == 0) {
-    int k = 0;
-    while (k < nm && P.maps[C.map_begin + k].kind == MAP_CHILD) ++k;
-    s_nchild = k;
-  }
-  for (int i = threadIdx.x; i < nm * W; i += kThreads) {
-    const int mi = i / W, c = i - mi * W;
-    const DMap mp = P.maps[C.map_begin + mi];
-    if (mp.kind == MAP_CHILD)
-      S.mval[i] = pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]));
-    else
-      S.mval[i] = __int_as_float(A.ev[((int64_t)tile * P.n_vars + mp.src) * W + c]);
-  }
-  __syncthreads();
-  const int nchild = s_nchild;
+  __syncwarp();
+  const int32_t R = (int32_t)C.R;
   const float *__restrict__ base = P.base32 + C.base_off;
-  float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W + lane * CPT;
-  const float *phs = A.phistar + lane * CPT;
-  int32_t *segA = S.segA + warp * nm;
+  float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
+  float *phi_out = A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
 
-  Vec<CPT> mx = vzero<CPT>();
-  auto load_segA = [&](int64_t s) {
-    for (int i = lane; i < nm; i += 32) segA[i] = __ldg(P.ipool + S.mA[i] + s);
+  int32_t s_first, u_first, count;
+  item_rows(it, R, s_first, u_first, count);
+  const int64_t e_first = (int64_t)s_first * R + u_first;  // rows are entries e_first + [0, count)
+  Vec<CPT> mx = vzero<CPT>(), acc = vzero<CPT>(), comp = vzero<CPT>(), part = vzero<CPT>();
+  for (int32_t b0 = 0; b0 < count; b0 += 32) {
+    const int nb = min(32, count - b0);
+    // lane j: indices of row b0 + j
+    const int64_t ej = e_first + b0 + min(lane, nb - 1);
+    const int32_t sj = (int32_t)(ej / R), uj = (int32_t)(ej - (int64_t)sj * R);
+    const float bj = __ldg(base + ej);
+    for (int i = 0; i < nm; ++i) idx[i * 32 + lane] = __ldg(P.ipool + mA[i] + sj) + __ldg(P.ipool + mB[i] + uj);
+    const unsigned last = __ballot_sync(kFull, !it.split && uj == R - 1 && lane < nb);
     __syncwarp();
-  };
-  auto rows = [&](int64_t s, int64_t ua, int64_t ub, Vec<CPT> &acc, Vec<CPT> &comp) {
-    const int64_t e0 = s * C.R;
-#pragma unroll 2
-    for (int64_t u = ua; u < ub; ++u) {
-      const int64_t e = e0 + u;
-      const float b = __ldg(base + e);
-      Vec<CPT> v;
+    for (int r = 0; r < nb; r += kGroup) {
+      Vec<CPT> v[kGroup];
 #pragma unroll
-      for (int k = 0; k < CPT; ++k) v.x[k] = b;
+      for (int g = 0; g < kGroup; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
       for (int i = 0; i < nchild; ++i) {
-        const int idx = segA[i] + __ldg(P.ipool + S.mB[i] + u);
-        const Vec<CPT> m = ld_plain<CPT>(phs + S.mrow[i] + (int64_t)idx * W);
-        const Vec<CPT> sc = ld_plain<CPT>(S.mval + i * W + lane * CPT);
+        const float *mp = A.phistar + mrow[i];
+        Vec<CPT> m[kGroup];
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) v.x[k] *= m.x[k] * sc.x[k];
+        for (int g = 0; g < kGroup; ++g) m[g] = ldrow<CPT, LD_NC>(mp + (int64_t)idx[i * 32 + min(r + g, nb - 1)] * W, lane);
+        const Vec<CPT> sc = ldrow<CPT>(mval + i * W, lane);
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g)
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) v[g].x[k] *= m[g].x[k] * sc.x[k];
       }
       for (int i = nchild; i < nm; ++i) {
-        const int d = segA[i] + __ldg(P.ipool + S.mB[i] + u);
+        int ev[CPT];
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-          const int ev = __float_as_int(S.mval[i * W + lane * CPT + k]);
-          if (ev >= 0 && ev != d) v.x[k] = 0.f;
+        for (int k = 0; k < CPT; ++k) ev[k] = __float_as_int(mval[i * W + col_of<CPT>(lane, k)]);
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g) {
+          const int d = idx[i * 32 + min(r + g, nb - 1)];
+#pragma unroll
+          for (int k = 0; k < CPT; ++k)
+            if (ev[k] >= 0 && ev[k] != d) v[g].x[k] = 0.f;
         }
       }
-      st_stream<CPT>(psi + e * W, v);
-      kahan_add<CPT>(acc, comp, v);
-    }
-  };
-  auto track_max = [&](const Vec<CPT> &m) {
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) mx.x[k] = fmaxf(mx.x[k], m.x[k]);
-  };
-
-  float *phi_out = A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W + lane * CPT;
-  if (!it.split) {
-    for (int64_t s = it.t0 + warp; s < it.t0 + it.nt; s += kWarps) {
-      load_segA(s);
-      Vec<CPT> acc = vzero<CPT>(), comp = vzero<CPT>();
-      rows(s, 0, C.R, acc, comp);
-      st_plain<CPT>(phi_out + s * W, acc);
-      track_max(acc);
-      __syncwarp();
-    }
-  } else {
-    const int64_t s = it.t0;
-    const int64_t q = (it.nu + kWarps - 1) / kWarps;
-    const int64_t ua = it.u0 + warp * q;
-    const int64_t ub = min(ua + q, it.u0 + it.nu);
-    load_segA(s);
-    Vec<CPT> acc = vzero<CPT>(), comp = vzero<CPT>();
-    if (ua < ub) rows(s, ua, ub, acc, comp);
-    st_plain<CPT>(S.red + warp * W + lane * CPT, acc);
-    __syncthreads();
-    if (warp == 0) {
-      Vec<CPT> tot = vzero<CPT>();
-      for (int w = 0; w < kWarps; ++w) {
-        const Vec<CPT> x = ld_plain<CPT>(S.red + w * W + lane * CPT);
+      for (int g = 0; g < kGroup; ++g) {
+        if (r + g < nb) {
+          strow<CPT, true>(psi + (e_first + b0 + r + g) * W, lane, v[g]);
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) tot.x[k] += x.x[k];
-      }
-      if (it.npieces == 1) {
-        st_plain<CPT>(phi_out + s * W, tot);
-        track_max(tot);
-      } else {
-        st_plain<CPT>(A.partial + ((int64_t)tile * P.n_partials + it.partial) * W + lane * CPT, tot);
-      }
-    }
-    if (it.npieces > 1) {
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned old = atomicAdd(&A.counters[(int64_t)tile * P.n_groups + it.group], 1u);
-        s_last = (old == (unsigned)(it.npieces - 1));
-      }
-      __syncthreads();
-      if (s_last && warp == 0) {
-        __threadfence();
-        const int first = it.partial - it.piece;
-        Vec<CPT> tot = vzero<CPT>();
-        for (int p = 0; p < it.npieces; ++p) {
-          const Vec<CPT> x = ld_cg<CPT>(A.partial + ((int64_t)tile * P.n_partials + first + p) * W + lane * CPT);
+          for (int k = 0; k < CPT; ++k) part.x[k] += v[g].x[k];
+          if ((last >> (r + g)) & 1u) {  // segment complete
+            kahan_fold<CPT>(acc, comp, part);
+            const int32_t s = __shfl_sync(kFull, sj, r + g);
+            strow<CPT>(phi_out + (int64_t)s * W, lane, acc);
 #pragma unroll
-          for (int k = 0; k < CPT; ++k) tot.x[k] += x.x[k];
+            for (int k = 0; k < CPT; ++k) mx.x[k] = fmaxf(mx.x[k], acc.x[k]);
+            acc = vzero<CPT>();
+            comp = vzero<CPT>();
+          }
         }
-        st_plain<CPT>(phi_out + s * W, tot);
-        track_max(tot);
-        if (lane == 0) A.counters[(int64_t)tile * P.n_groups + it.group] = 0u;
       }
+      kahan_fold<CPT>(acc, comp, part);
+    }
+    __syncwarp();
+  }
+  if (it.split) {
+    Vec<CPT> tot;
+    if (combine_split<CPT>(it, P, A, tile, lane, acc, tot)) {
+      strow<CPT>(phi_out + it.t0 * W, lane, tot);
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) mx.x[k] = fmaxf(mx.x[k], tot.x[k]);
     }
   }
-  // per-case maximum of the message entries this block completed
-  st_plain<CPT>(S.redm + warp * W + lane * CPT, mx);
-  __syncthreads();
-  if (warp == 0) {
-    Vec<CPT> m = vzero<CPT>();
-    for (int w = 0; w < kWarps; ++w) {
-      const Vec<CPT> x = ld_plain<CPT>(S.redm + w * W + lane * CPT);
+  // per-case maximum of the message entries this warp completed
+  unsigned *mb = A.maxbits + ((int64_t)tile * P.n_cliques + it.task) * W;
 #pragma unroll
-      for (int k = 0; k < CPT; ++k) m.x[k] = fmaxf(m.x[k], x.x[k]);
-    }
-    unsigned *mb = A.maxbits + ((int64_t)tile * P.n_cliques + it.task) * W + lane * CPT;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k)
-      if (m.x[k] > 0.f) atomicMax(mb + k, __float_as_uint(m.x[k]));
-  }
+  for (int k = 0; k < CPT; ++k)
+    if (mx.x[k] > 0.f) atomicMax(mb + col_of<CPT>(lane, k), __float_as_uint(mx.x[k]));
 }
 
 // ---------------------------------------------------------------------------
 // distribute
 // ---------------------------------------------------------------------------
 template <int CPT>
-__global__ void __launch_bounds__(kThreads) k_distribute(DevPlan P, DevArena A, int64_t item_begin) {
+__global__ void __launch_bounds__(kThreads, 2) k_distribute(DevPlan P, DevArena A, int64_t item_begin,
+                                                             int64_t n_items) {
   constexpr int W = 32 * CPT;
-  __shared__ __align__(16) float red[kWarps * W];
-  __shared__ int s_last;
-  const DItem it = P.ditems[item_begin + blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (iw >= n_items) return;
+  const DItem it = P.ditems[item_begin + iw];
   const int tile = blockIdx.y;
   const DTask T = P.tasks[it.task];
   const DClique C = P.cl[T.clique];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W + lane * CPT;
-  const float *rho = A.rho + ((int64_t)tile * P.sep_rows + C.sep_row) * W + lane * CPT;
-  const bool root = C.is_root != 0;
+  // X rows: the clique's psi, or the phi* rows of its upward separator
+  const float *psi = T.src_sep ? A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W
+                               : A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
+  const float *rho = A.rho + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
+  const bool root = !T.src_sep && C.is_root != 0;
   Vec<CPT> rs;
 #pragma unroll
   for (int k = 0; k < CPT; ++k)
-    rs.x[k] = root ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + lane * CPT + k]))
+    rs.x[k] = root ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + col_of<CPT>(lane, k)]))
                    : 1.f;
+  const int32_t *__restrict__ At = P.ipool + T.A_off;
+  const int32_t *__restrict__ sAt = P.ipool + T.sA_off;
   const int32_t *__restrict__ Bt = P.ipool + T.B_off;
   const int32_t *__restrict__ sBt = P.ipool + T.sB_off;
+  const int32_t U = (int32_t)T.U;
 
-  auto rows = [&](int64_t t, int64_t ua, int64_t ub, Vec<CPT> &acc, Vec<CPT> &comp) {
-    const int64_t a = __ldg(P.ipool + T.A_off + t);
-    const int64_t sa = __ldg(P.ipool + T.sA_off + t);
-    if (root) {
-#pragma unroll 4
-      for (int64_t u = ua; u < ub; ++u) {
-        const Vec<CPT> p = ld_stream<CPT>(psi + (a + __ldg(Bt + u)) * W);
-        Vec<CPT> v;
-#pragma unroll
-        for (int k = 0; k < CPT; ++k) v.x[k] = p.x[k] * rs.x[k];
-        kahan_add<CPT>(acc, comp, v);
-      }
-    } else {
-#pragma unroll 4
-      for (int64_t u = ua; u < ub; ++u) {
-        const Vec<CPT> p = ld_stream<CPT>(psi + (a + __ldg(Bt + u)) * W);
-        const Vec<CPT> r = ld_plain<CPT>(rho + (sa + __ldg(sBt + u)) * W);
-        Vec<CPT> v;
-#pragma unroll
-        for (int k = 0; k < CPT; ++k) v.x[k] = p.x[k] * r.x[k];
-        kahan_add<CPT>(acc, comp, v);
-      }
-    }
-  };
   auto output = [&](int64_t t, const Vec<CPT> &val) {
     if (T.kind == TASK_CHILD) {
-      const int64_t o = ((int64_t)tile * P.sep_rows + T.dst_row + t) * W + lane * CPT;
-      const Vec<CPT> ph = ld_plain<CPT>(A.phistar + o);
-      Vec<CPT> r;
+      const int64_t o = ((int64_t)tile * P.sep_rows + T.dst_row + t) * W;
+      const Vec<CPT> ph = ldrow<CPT>(A.phistar + o, lane);
+      Vec<CPT> q;
 #pragma unroll
-      for (int k = 0; k < CPT; ++k) r.x[k] = (ph.x[k] > 0.f) ? val.x[k] / ph.x[k] : 0.f;  // 0/0 := 0
-      st_plain<CPT>(A.rho + o, r);
+      for (int k = 0; k < CPT; ++k) q.x[k] = (ph.x[k] > 0.f) ? val.x[k] / ph.x[k] : 0.f;  // 0/0 := 0
+      strow<CPT>(A.rho + o, lane, q);
     } else {
-      st_plain<CPT>(A.post + ((int64_t)tile * P.post_rows + T.dst_row + t) * W + lane * CPT, val);
+      strow<CPT>(A.post + ((int64_t)tile * P.post_rows + T.dst_row + t) * W, lane, val);
     }
   };
 
-  if (!it.split) {
-    for (int64_t t = it.t0 + warp; t < it.t0 + it.nt; t += kWarps) {
-      Vec<CPT> acc = vzero<CPT>(), comp = vzero<CPT>();
-      rows(t, 0, T.U, acc, comp);
-      output(t, acc);
-    }
-  } else {
-    const int64_t t = it.t0;
-    const int64_t q = (it.nu + kWarps - 1) / kWarps;
-    const int64_t ua = it.u0 + warp * q;
-    const int64_t ub = min(ua + q, it.u0 + it.nu);
-    Vec<CPT> acc = vzero<CPT>(), comp = vzero<CPT>();
-    if (ua < ub) rows(t, ua, ub, acc, comp);
-    st_plain<CPT>(red + warp * W + lane * CPT, acc);
-    __syncthreads();
-    if (warp == 0) {
-      Vec<CPT> tot = vzero<CPT>();
-      for (int w = 0; w < kWarps; ++w) {
-        const Vec<CPT> x = ld_plain<CPT>(red + w * W + lane * CPT);
+  int32_t t_first, u_first, count;
+  item_rows(it, U, t_first, u_first, count);
+  Vec<CPT> acc = vzero<CPT>(), comp = vzero<CPT>(), part = vzero<CPT>();
+  for (int32_t b0 = 0; b0 < count; b0 += 32) {
+    const int nb = min(32, count - b0);
+    // lane j: indices of row b0 + j, rows flattened as (t, u)
+    const int32_t f = u_first + b0 + min(lane, nb - 1);
+    const int32_t tj = t_first + f / U, uj = f - (f / U) * U;
+    const int32_t ej = __ldg(At + tj) + __ldg(Bt + uj);
+    const int32_t xj = root ? 0 : __ldg(sAt + tj) + __ldg(sBt + uj);
+    const unsigned last = __ballot_sync(kFull, !it.split && uj == U - 1 && lane < nb);
+    for (int r = 0; r < nb; r += kGroup) {
+      Vec<CPT> p[kGroup];
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) tot.x[k] += x.x[k];
-      }
-      if (it.npieces == 1)
-        output(t, tot);
-      else
-        st_plain<CPT>(A.partial + ((int64_t)tile * P.n_partials + it.partial) * W + lane * CPT, tot);
-    }
-    if (it.npieces > 1) {
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned old = atomicAdd(&A.counters[(int64_t)tile * P.n_groups + it.group], 1u);
-        s_last = (old == (unsigned)(it.npieces - 1));
-      }
-      __syncthreads();
-      if (s_last && warp == 0) {
-        __threadfence();
-        const int first = it.partial - it.piece;
-        Vec<CPT> tot = vzero<CPT>();
-        for (int p = 0; p < it.npieces; ++p) {
-          const Vec<CPT> x = ld_cg<CPT>(A.partial + ((int64_t)tile * P.n_partials + first + p) * W + lane * CPT);
+      for (int g = 0; g < kGroup; ++g)
+        p[g] = ldrow<CPT, LD_STREAM>(psi + (int64_t)__shfl_sync(kFull, ej, min(r + g, nb - 1)) * W, lane);
+      if (!root) {
+        Vec<CPT> q[kGroup];
 #pragma unroll
-          for (int k = 0; k < CPT; ++k) tot.x[k] += x.x[k];
+        for (int g = 0; g < kGroup; ++g)
+          q[g] = ldrow<CPT, LD_NC>(rho + (int64_t)__shfl_sync(kFull, xj, min(r + g, nb - 1)) * W, lane);
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g)
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) p[g].x[k] *= q[g].x[k];
+      } else {
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g)
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) p[g].x[k] *= rs.x[k];
+      }
+#pragma unroll
+      for (int g = 0; g < kGroup; ++g) {
+        if (r + g < nb) {
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) part.x[k] += p[g].x[k];
+          if ((last >> (r + g)) & 1u) {  // target entry complete
+            kahan_fold<CPT>(acc, comp, part);
+            output(__shfl_sync(kFull, tj, r + g), acc);
+            acc = vzero<CPT>();
+            comp = vzero<CPT>();
+          }
         }
-        output(t, tot);
-        if (lane == 0) A.counters[(int64_t)tile * P.n_groups + it.group] = 0u;
       }
+      kahan_fold<CPT>(acc, comp, part);
     }
+  }
+  if (it.split) {
+    Vec<CPT> tot;
+    if (combine_split<CPT>(it, P, A, tile, lane, acc, tot)) output(it.t0, tot);
   }
 }
 
 // ---------------------------------------------------------------------------
-// finalize: one warp per case
+// finalize, part 1: log P(e) and status, one thread per case
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(DevPlan P, DevArena A, int W, int32_t n_cases, int64_t root_sep_row,
-                           double *__restrict__ log_pe, double *__restrict__ post,
-                           int32_t *__restrict__ status) {
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= n_cases) return;
-  const int64_t tile = wid / W;
-  const int c = (int)(wid % W);
+constexpr int kStageCols = 16;
+
+__global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *__restrict__ log_pe,
+                        int32_t *__restrict__ status) {
+  const int tile = blockIdx.x;
+  const int c = threadIdx.x;
+  const int64_t cs = (int64_t)tile * W + c;
+  if (cs >= n_cases) return;
   // Messages multiplied into a parent were scaled by 2^-k: add k back.
   // Every component root contributes the log of its total -- except a
   // component without any observed variable, whose probability is exactly 1
-  // (a sum over all states of a product of CPTs) and contributes 0; its
-  // cliques' exponents are left out with it.
+  // (a sum over all states of a product of CPTs) and contributes 0.
   long long K = 0;
   double lz = 0.0;
   int zero = 0;
-  for (int cl = lane; cl < P.n_cliques; cl += 32) {
-    const DClique &D = P.cl[cl];
-    if (!D.is_root) continue;
+  for (int q = 0; q < P.n_comp; ++q) {
+    const int cl = P.comp_roots[q];
     bool observed = false;
     for (int k = P.comp_ptr[cl]; k < P.comp_ptr[cl + 1] && !observed; ++k)
-      observed = A.ev[(tile * P.n_vars + P.comp_vars[k]) * W + c] >= 0;
+      observed = A.ev[((int64_t)tile * P.n_vars + P.comp_vars[k]) * W + c] >= 0;
     if (!observed) continue;
-    const float z = A.phistar[(tile * P.sep_rows + D.sep_row) * W + c];
+    const DClique &D = P.cl[cl];
+    const float z = A.phistar[((int64_t)tile * P.sep_rows + D.sep_row) * W + c];
     if (z > 0.f) lz += log((double)z); else zero = 1;
     K += D.comp_base_exp;
     for (int k = D.comp_begin; k < D.comp_end; ++k)
-      K += pow2_exp(A.maxbits[(tile * P.n_cliques + P.comp_cliques[k]) * W + c]);
+      K += pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + P.comp_cliques[k]) * W + c]);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    K += __shfl_xor_sync(0xffffffffu, K, o);
-    lz += __shfl_xor_sync(0xffffffffu, lz, o);
-    zero |= __shfl_xor_sync(0xffffffffu, zero, o);
-  }
-  (void)root_sep_row;
-  const int bad = A.bad[tile * W + c];
+  const int bad = A.bad[cs];
   const int st = bad ? JT_CASE_BAD_EVIDENCE : (zero ? JT_CASE_ZERO_EVIDENCE : JT_CASE_OK);
-  if (lane == 0) {
-    double lp;
-    if (st == JT_CASE_OK)
-      lp = lz + (double)K * 0.69314718055994530942;
-    else if (st == JT_CASE_ZERO_EVIDENCE)
-      lp = -INFINITY;
-    else
-      lp = NAN;
-    log_pe[wid] = lp;
-    status[wid] = st;
-  }
-  double *out = post + wid * P.post_rows;
-  for (int v = lane; v < P.n_vars; v += 32) {
+  double lp;
+  if (st == JT_CASE_OK) lp = lz + (double)K * 0.69314718055994530942;
+  else if (st == JT_CASE_ZERO_EVIDENCE) lp = -INFINITY;
+  else lp = NAN;
+  log_pe[cs] = lp;
+  status[cs] = st;
+}
+
+// ---------------------------------------------------------------------------
+// finalize, part 2: FP64 posterior normalisation.  Block (tile, variable
+// group), one thread per case; values are staged in shared memory and
+// written out row by row so that global writes are contiguous.
+// ---------------------------------------------------------------------------
+__global__ void k_posterior(DevPlan P, DevArena A, int W, int32_t n_cases, const int32_t *__restrict__ status,
+                            double *__restrict__ post) {
+  extern __shared__ double stage[];  // [W][kStageCols + 1]
+  const int tile = blockIdx.x;
+  const int c = threadIdx.x;
+  const int64_t cs = (int64_t)tile * W + c;
+  const int64_t left = (int64_t)n_cases - (int64_t)tile * W;
+  const int rows_here = (int)(left < W ? left : W);
+  const int st = cs < n_cases ? status[cs] : JT_CASE_BAD_EVIDENCE;
+  const int v0 = P.pgroup_ptr[blockIdx.y], v1 = P.pgroup_ptr[blockIdx.y + 1];
+  int64_t col0 = P.post_off[v0];  // first column of the staged block
+  auto flush = [&](int ncols) {
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int rr = warp; rr < rows_here; rr += nw)
+      for (int j = lane; j < ncols; j += 32)
+        post[((int64_t)tile * W + rr) * P.post_rows + col0 + j] = stage[rr * (kStageCols + 1) + j];
+    __syncthreads();
+  };
+  for (int v = v0; v < v1; ++v) {
     const int64_t off = P.post_off[v];
     const int r = P.card[v];
-    const int ev = A.ev[(tile * P.n_vars + v) * W + c];
-    if (st != JT_CASE_OK) {
-      for (int j = 0; j < r; ++j) out[off + j] = NAN;
-    } else if (ev >= 0) {
-      for (int j = 0; j < r; ++j) out[off + j] = (j == ev) ? 1.0 : 0.0;
-    } else {
-      const float *m = A.post + (tile * P.post_rows + off) * W + c;
-      double s = 0.0;
+    const int ev = A.ev[((int64_t)tile * P.n_vars + v) * W + c];
+    const float *m = A.post + ((int64_t)tile * P.post_rows + off) * W + c;
+    double s = 0.0;
+    if (st == JT_CASE_OK && ev < 0)
       for (int j = 0; j < r; ++j) s += (double)m[(int64_t)j * W];
-      for (int j = 0; j < r; ++j) out[off + j] = (double)m[(int64_t)j * W] / s;
+    for (int j = 0; j < r; ++j) {
+      if (off + j - col0 == kStageCols) {
+        flush(kStageCols);
+        col0 += kStageCols;
+      }
+      double val;
+      if (st != JT_CASE_OK) val = NAN;
+      else if (ev >= 0) val = (j == ev) ? 1.0 : 0.0;
+      else val = (double)m[(int64_t)j * W] / s;
+      stage[c * (kStageCols + 1) + (off + j - col0)] = val;
     }
   }
+  flush((int)(P.post_off[v1 - 1] + P.card[v1 - 1] - col0));
 }
 
 // ---------------------------------------------------------------------------
@@ -596,7 +603,10 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
-size_t collect_smem_bytes(int cpt, int max_maps) { return collect_smem_layout(cpt, max_maps, nullptr, nullptr); }
+size_t collect_smem_bytes(int cpt, int max_maps) {
+  return std::min<size_t>(kWarps * collect_warp_smem(cpt, max_maps), kCollectSmemLimit);
+}
+size_t collect_warp_smem_bytes(int cpt, int max_maps) { return collect_warp_smem(cpt, max_maps); }
 
 void launch_evidence(int cpt, const int32_t *d_ev_in, int32_t n_cases, const DevPlan &P,
                      const DevArena &A, cudaStream_t s) {
@@ -606,15 +616,24 @@ void launch_evidence(int cpt, const int32_t *d_ev_in, int32_t n_cases, const Dev
   k_evidence<<<blocks, 256, 0, s>>>(d_ev_in, n_cases, P, A, W);
 }
 
+// Warps per collect block: eight, fewer when a layer's cliques carry so many
+// maps that eight warps' shared memory would not fit.
+static int collect_warps(int cpt, int max_maps) {
+  const size_t per_warp = collect_warp_smem(cpt, max_maps);
+  return (int)std::min<size_t>(kWarps, std::max<size_t>(1, kCollectSmemLimit / std::max<size_t>(per_warp, 1)));
+}
+
 template <int CPT>
 static void collect_t(const DevPlan &P, const DevArena &A, int64_t b, int64_t n, int max_maps, cudaStream_t s) {
-  const size_t smem = collect_smem_bytes(CPT, max_maps);
-  dim3 grid((unsigned)n, (unsigned)A.tiles);
-  k_collect<CPT><<<grid, kThreads, smem, s>>>(P, A, b);
+  const int nw = collect_warps(CPT, max_maps);
+  const size_t smem = (size_t)nw * collect_warp_smem(CPT, max_maps);
+  dim3 grid((unsigned)((n + nw - 1) / nw), (unsigned)A.tiles);
+  k_collect<CPT><<<grid, 32 * nw, smem, s>>>(P, A, b, n, max_maps);
 }
 
 cudaError_t configure_collect_smem(int cpt, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
+  if (cpt == 8) return cudaFuncSetAttribute(k_collect<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (cpt == 4) return cudaFuncSetAttribute(k_collect<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (cpt == 2) return cudaFuncSetAttribute(k_collect<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaFuncSetAttribute(k_collect<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -623,17 +642,24 @@ cudaError_t configure_collect_smem(int cpt, size_t bytes) {
 void launch_collect(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, int max_maps,
                     cudaStream_t s) {
   if (n <= 0) return;
-  if (cpt == 4) collect_t<4>(P, A, b, n, max_maps, s);
+  if (cpt == 8) collect_t<8>(P, A, b, n, max_maps, s);
+  else if (cpt == 4) collect_t<4>(P, A, b, n, max_maps, s);
   else if (cpt == 2) collect_t<2>(P, A, b, n, max_maps, s);
   else collect_t<1>(P, A, b, n, max_maps, s);
 }
 
 void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  dim3 grid((unsigned)n, (unsigned)A.tiles);
-  if (cpt == 4) k_distribute<4><<<grid, kThreads, 0, s>>>(P, A, b);
-  else if (cpt == 2) k_distribute<2><<<grid, kThreads, 0, s>>>(P, A, b);
-  else k_distribute<1><<<grid, kThreads, 0, s>>>(P, A, b);
+  dim3 grid((unsigned)((n + kWarps - 1) / kWarps), (unsigned)A.tiles);
+  if (cpt == 8) k_distribute<8><<<grid, kThreads, 0, s>>>(P, A, b, n);
+  else if (cpt == 4) k_distribute<4><<<grid, kThreads, 0, s>>>(P, A, b, n);
+  else if (cpt == 2) k_distribute<2><<<grid, kThreads, 0, s>>>(P, A, b, n);
+  else k_distribute<1><<<grid, kThreads, 0, s>>>(P, A, b, n);
+}
+
+cudaError_t configure_distribute_smem(int cpt) {
+  (void)cpt;  // the distribute kernel uses static shared memory only
+  return cudaSuccess;
 }
 
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,
@@ -658,13 +684,15 @@ void launch_plain_finalize(const double *pe, const double *marg, const int32_t *
 }
 
 void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cases,
-                            int64_t root_sep_row, double *d_log_pe, double *d_post, int32_t *d_status,
-                            cudaStream_t s) {
+                     int64_t root_sep_row, double *d_log_pe, double *d_post, int32_t *d_status,
+                     cudaStream_t s) {
+  (void)root_sep_row;
   if (n_cases <= 0) return;
   const int W = 32 * cpt;
-  const int threads = 256;
-  const unsigned blocks = blocks_for((int64_t)n_cases * 32, threads);
-  k_finalize<<<blocks, threads, 0, s>>>(P, A, W, n_cases, root_sep_row, d_log_pe, d_post, d_status);
+  const unsigned tiles = (unsigned)((n_cases + W - 1) / W);
+  k_logpe<<<tiles, W, 0, s>>>(P, A, W, n_cases, d_log_pe, d_status);
+  const size_t smem = sizeof(double) * (size_t)W * (kStageCols + 1);
+  k_posterior<<<dim3(tiles, (unsigned)P.n_pgroups), W, smem, s>>>(P, A, W, n_cases, d_status, d_post);
 }
 
 }  // namespace jt

@@ -7,7 +7,7 @@
 
 namespace jt {
 
-constexpr int kWarps = 8;               // warps per thread block of a layer launch
+constexpr int kWarps = 8;               // warps (independent work items) per block of a layer launch
 constexpr int kThreads = 32 * kWarps;
 
 struct DevPlan {
@@ -23,6 +23,10 @@ struct DevPlan {
   const int32_t *comp_ptr;   // [n_cliques + 1] variables of the component rooted at a clique
   const int32_t *comp_vars;  // [n]
   const int32_t *comp_cliques;  // non-root cliques of each component
+  const int32_t *comp_roots;    // [n_comp] component root cliques
+  const int32_t *pgroup_ptr;    // [n_pgroups + 1] variable groups of the posterior kernel
+  int32_t n_comp;
+  int32_t n_pgroups;
   int32_t n_vars;
   int32_t n_cliques;
   int32_t root;
@@ -46,6 +50,7 @@ struct DevArena {
   uint32_t *counters;  // [tile][group] pieces finished
   int32_t *ev;         // [tile][var][W] evidence, -1 = unobserved
   int32_t *bad;        // [tile * W] 1 = invalid evidence
+  uint32_t *errflag;   // one word per arena: nonzero after a bounded device wait expired
   int32_t tiles;       // tiles in this chunk
 };
 
@@ -59,9 +64,12 @@ void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t ite
 void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cases,
                      int64_t root_sep_row, double *d_log_pe, double *d_post, int32_t *d_status,
                      cudaStream_t s);
-size_t collect_smem_bytes(int cpt, int max_maps);
-// raise the dynamic shared-memory limit of the collect kernel (once per plan)
+size_t collect_smem_bytes(int cpt, int max_maps);        // block (capped at kCollectSmemLimit)
+size_t collect_warp_smem_bytes(int cpt, int max_maps);   // one warp
+constexpr size_t kCollectSmemLimit = 220 * 1024;
+// raise the dynamic shared-memory limits of the layer kernels (once per plan)
 cudaError_t configure_collect_smem(int cpt, size_t bytes);
+cudaError_t configure_distribute_smem(int cpt);
 constexpr int kMaxTilesPerChunk = 16384;
 
 // plain FP64 path

@@ -60,7 +60,7 @@ extern "C" jt_status jt_infer_device_noalloc(jt_plan *pl, int32_t n_cases, const
   if (!d_ev || !d_lp || !d_post || !d_st) { set_error("null buffer"); return JT_EINVAL; }
   const Plan &P = pl->P;
   const ArenaLayout L = arena_layout(P);
-  if (L.per_tile > kScratchBytes) {
+  if (L.bytes(1) > kScratchBytes) {
     set_error("this plan needs " + std::to_string(L.per_tile) + " bytes of scratch per case tile; "
               "the static scratch holds " + std::to_string(kScratchBytes) + " bytes");
     return JT_ENOMEM;
@@ -73,7 +73,8 @@ extern "C" jt_status jt_infer_device_noalloc(jt_plan *pl, int32_t n_cases, const
   void *scratch = nullptr;
   jt_status st = scratch_for(pl->device, &scratch);
   if (st != JT_OK) return st;
-  const int tiles = (int)std::min<size_t>(kScratchBytes / L.per_tile, (size_t)kMaxTilesPerChunk);
+  const int tiles =
+      (int)std::min<size_t>((kScratchBytes - ArenaLayout::kTail) / L.per_tile, (size_t)kMaxTilesPerChunk);
   Arena a;
   st = arena_wrap(P, a, scratch, kScratchBytes, tiles);
   if (st != JT_OK) return st;
@@ -81,8 +82,10 @@ extern "C" jt_status jt_infer_device_noalloc(jt_plan *pl, int32_t n_cases, const
   const int W = P.tile;
   const int64_t chunk = (int64_t)tiles * W;
   // the array keeps the previous call's contents: the split-sum counters
-  // must start at zero (the other per-chunk state is cleared below)
-  if (cudaMemsetAsync(a.da.counters, 0, L.counters * (size_t)tiles, s) != cudaSuccess) {
+  // and the error flag must start at zero (the other per-chunk state is
+  // cleared below)
+  if (cudaMemsetAsync(a.da.counters, 0, L.counters * (size_t)tiles, s) != cudaSuccess ||
+      cudaMemsetAsync(a.da.errflag, 0, sizeof(uint32_t), s) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMemsetAsync on the static scratch failed");
     return JT_ECUDA;

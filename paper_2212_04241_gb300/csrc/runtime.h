@@ -14,6 +14,8 @@ namespace jt {
 struct ArenaLayout {
   size_t psi, sep, post, partial, maxbits, counters, ev, bad;
   size_t per_tile;
+  static constexpr size_t kTail = 256;  // once per arena: the error flag
+  size_t bytes(int tiles) const { return per_tile * (size_t)tiles + kTail; }
 };
 
 // Device memory for the per-batch tables of up to `tiles` case tiles, and
@@ -64,5 +66,8 @@ struct jt_plan {
 namespace jt {
 jt_status run_chunk(jt_plan *pl, Arena &a, const int32_t *d_ev, int32_t nc, double *d_lp, double *d_post,
                     int32_t *d_st, cudaStream_t s);
+// JT_ETIMEOUT (and the flag cleared) when a kernel reported an expired
+// bounded wait on this arena; call after synchronising its stream
+jt_status check_arena_flag(Arena &a);
 int budget_tiles(const jt_plan *pl, int64_t budget_bytes);
 }  // namespace jt

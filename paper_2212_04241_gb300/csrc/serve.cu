@@ -103,7 +103,7 @@ size_t slot_bytes(const jt_plan *pl, int max_batch, size_t *io_bytes) {
   const size_t io = sizeof(int32_t) * (size_t)max_batch * P.n + sizeof(double) * max_batch +
                     sizeof(double) * (size_t)max_batch * P.sum_card + sizeof(int32_t) * max_batch + 4 * 256;
   if (io_bytes) *io_bytes = io;
-  return arena_layout(P).per_tile * (size_t)tiles + io;
+  return arena_layout(P).bytes(tiles) + io;
 }
 
 bool slot_create(jt_server *S, int plan_id, Slot &s) {

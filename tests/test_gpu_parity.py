@@ -43,7 +43,7 @@ def test_bn20_plain_all_cases():
     np.testing.assert_allclose(post, opost, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("cpt", [1, 2, 4])
+@pytest.mark.parametrize("cpt", [1, 2, 4, 8])
 def test_bn20_batched_all_cases(cpt):
     net = configs.network("bn20")
     ev = configs.evidence("bn20", net)
@@ -60,7 +60,7 @@ def test_bn60_full_batch_all_cases():
     print(f"bn60 max posterior err {perr:.3g}, log P(e) err {lerr:.3g}")
 
 
-@pytest.mark.parametrize("opts", [dict(cases_per_thread=1), dict(cases_per_thread=2),
+@pytest.mark.parametrize("opts", [dict(cases_per_thread=1), dict(cases_per_thread=2), dict(cases_per_thread=4),
                                   dict(use_graphs=0), dict(root_rule=J.JT_ROOT_LARGEST),
                                   dict(rows_per_cta=64), dict(rows_per_cta=4096)])
 def test_bn60_option_variants(opts):
@@ -103,7 +103,7 @@ def test_result_independent_of_batch_position():
     ev = configs.evidence("bn60", net, n_cases=700)
     p = J.Plan(net)
     lp, post, st = p.infer(ev)
-    for i in (0, 5, 127, 128, 699):
+    for i in (0, 5, 127, 128, 255, 256, 699):
         a = p.infer(ev[i:i + 1])
         assert a[0][0] == lp[i] and np.array_equal(a[1][0], post[i])
     perm = np.random.default_rng(0).permutation(700)
@@ -111,7 +111,7 @@ def test_result_independent_of_batch_position():
     assert np.array_equal(b[0], lp[perm]) and np.array_equal(b[1], post[perm])
 
 
-@pytest.mark.parametrize("n_cases", [0, 1, 31, 127, 129, 257])
+@pytest.mark.parametrize("n_cases", [0, 1, 31, 127, 129, 255, 257, 513])
 def test_ragged_and_empty_batches(n_cases):
     net = configs.network("bn60")
     ev = configs.evidence("bn60", net, n_cases=max(n_cases, 1))[:n_cases]
