@@ -147,6 +147,74 @@ def _oracle_rate(net, ev, threads, budget_s):
     return done / dt, done, dt
 
 
+SERVING_PLANS = ["bn60", "bn110", "bn420", "bn1000"]
+
+
+def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, max_batch: int = 64,
+                arena_gb: float = 48.0):
+    """The serving mix: resident plans of the four networks, one-case requests
+    on a uniformly chosen plan with 5-30 % observed, Poisson arrivals at
+    fractions of the measured saturated rate.  Returns p50/p99 latency
+    (submit -> result on the host) and cases/s per offered rate."""
+    import paper_2212_04241_gb300.jt as J
+    from synth import configs
+    from synth.bn import sample_cases
+    rng = np.random.default_rng(seed)
+    nets = [configs.network(nm) for nm in SERVING_PLANS]
+    plans = [J.Plan(n, cases_per_thread=1) for n in nets]
+    pool = [sample_cases(n, 2048, (0.05, 0.30), seed + i) for i, n in enumerate(nets)]
+
+    def drive(srv, pids, n_req, rate):
+        """Submit n_req requests (Poisson at `rate`/s, or all at once if rate
+        is None), wait for all, return wall seconds."""
+        which = rng.integers(0, len(plans), size=n_req)
+        rows = rng.integers(0, 2048, size=n_req)
+        gaps = rng.exponential(1.0 / rate, size=n_req) if rate else np.zeros(n_req)
+        tickets = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(n_req):
+            t_next += gaps[i]
+            while rate and time.perf_counter() < t_next:
+                pass
+            p = int(which[i])
+            tickets.append((srv.submit(pids[p], pool[p][rows[i]]), plans[p].sum_card))
+        srv.drain()
+        dt = time.perf_counter() - t0
+        for t, m in tickets:
+            r = srv.poll(t, m)
+            assert r is not None
+        return dt
+
+    def fresh():
+        srv = J.Server(arena_bytes=int(arena_gb * (1 << 30)), max_batch=max_batch, max_inflight=8)
+        return srv, [srv.add_plan(pl) for pl in plans]
+
+    srv, pids = fresh()
+    drive(srv, pids, 2000, None)  # warm-up: slots, graphs
+    n_sat = 20000
+    sat = n_sat / drive(srv, pids, n_sat, None)
+    srv.close()
+    out = {"plans": SERVING_PLANS, "max_batch": max_batch, "arena_gb": arena_gb,
+           "saturated_cases_per_s": sat, "rates": []}
+    for f in rates:
+        rate = f * sat
+        n_req = int(max(2000, min(200000, rate * duration_s)))
+        srv, pids = fresh()
+        drive(srv, pids, 500, None)
+        srv.close()
+        srv, pids = fresh()
+        dt = drive(srv, pids, n_req, rate)
+        st = srv.stats()
+        srv.close()
+        out["rates"].append({"offered_fraction": f, "offered_cases_per_s": rate, "requests": n_req,
+                             "achieved_cases_per_s": n_req / dt, "p50_ms": st["p50_ns"] / 1e6,
+                             "p99_ms": st["p99_ns"] / 1e6, "batches": st["batches"],
+                             "largest_batch": st["largest_batch"],
+                             "peak_arena_gb": st["peak_arena_bytes"] / 2**30})
+    return out
+
+
 def run_reference(args, name, net, ev, rank, world):
     if rank != 0:
         return 0
@@ -189,6 +257,9 @@ def main():
     ap.add_argument("--cases", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix latency measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="default plan options instead of jt_autotune")
+    ap.add_argument("--serving-only", action="store_true", help="only the serving-mix measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -207,6 +278,9 @@ def main():
         return run_reference(args, name, net, ev, rank, world)
 
     import torch
+    if args.serving_only:
+        print(json.dumps({"serving": run_serving()}), flush=True)
+        return 0
     torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
@@ -214,7 +288,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     import paper_2212_04241_gb300.jt as J
-    plan = J.Plan(net)
+    # the library's autotuner picks the tile shape for this network and batch
+    tuned, _ = J.autotune(net, n_cases) if not args.no_autotune else ({}, None)
+    plan = J.Plan(net, **tuned)
     stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
     d_ev = torch.from_numpy(ev).cuda()
@@ -324,6 +400,10 @@ def main():
         cpu = {"value": rate, "unit": "cases/s", "cores": cores, "kind": "oracle",
                "sample": f"{done} cases of the workload in {dt:.1f} s"}
 
+    serving = None
+    if rank == 0 and not args.no_serving and world == 1:
+        serving = run_serving()
+
     if dist:
         dist.destroy_process_group()
     if rank != 0:
@@ -336,12 +416,13 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[name], "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
                    "chunk_cases": info["chunk_cases"], "levels": info["n_levels"],
+                   "autotuned": {k: tuned[k] for k in ("cases_per_thread", "items_per_tile")} if tuned else None,
                    "sum_clique_entries": info["sum_clique_entries"],
                    "l2": "inputs larger than L2 (psi arena %.2f GB per step)" % (4.0 * info["sum_clique_entries"] * n_cases / 1e9),
                    "parallelism": f"cases sharded, {world} rank(s)"},
         "gpu_launches": int(launches * args.steps),
         "roofline": roofline, "clocks": clock_info, "e2e": e2e, "plain_gpu": plain,
-        "cpu_baseline": cpu, "accuracy": accuracy,
+        "cpu_baseline": cpu, "accuracy": accuracy, "serving": serving,
     }
     print(json.dumps(line), flush=True)
     return 0

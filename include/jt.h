@@ -92,10 +92,14 @@ typedef struct {
   int64_t max_clique_entries; /* JT_ETOOBIG above this; 0 = 2^31 - 1 */
   int64_t arena_bytes;        /* device bytes for per-batch tables; the
                                  batch is processed in chunks that fit;
-                                 0 = automatic (min(96 GiB, 60% of free)) */
+                                 0 = automatic (min(224 GiB, 70% of free)) */
   int32_t use_graphs;         /* 1 (default): replay the layer launches of a
                                  batch chunk as one captured CUDA graph */
-  int32_t reserved[7];
+  int32_t items_per_tile;     /* target warp work items per case tile and
+                                 tree layer when rows_per_cta is 0: small
+                                 values give long items, large values short
+                                 ones; 0 = automatic (192) */
+  int32_t reserved[6];
 } jt_compile_opts;
 
 typedef struct {
@@ -213,6 +217,19 @@ JT_API jt_status jt_infer_plain(jt_plan *plan, int32_t n_cases, const int32_t *e
 JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evidence,
                             double *d_log_pe, double *d_posteriors, int32_t *d_case_status,
                             void *cuda_stream, double *out);
+
+/*
+ * Autotuner (no counterpart in the paper): compiles the network with each
+ * candidate tile shape -- cases per thread in {4, 8} and work items per
+ * tile and layer in {96, 192, 384} -- times batched inference of n_cases
+ * cases on the current device (CUDA events, one warm-up and three timed
+ * runs each), and writes the fastest options to *best (base fields kept)
+ * and its time per case in ns to *best_ns_per_case (may be NULL).  base may
+ * be NULL for the defaults.  Allocates and frees its own device memory.
+ */
+JT_API jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
+                             const int32_t *parents, const double *cpt, const jt_compile_opts *base,
+                             int32_t n_cases, jt_compile_opts *best, double *best_ns_per_case);
 
 /* Sizes and layout of a compiled plan. */
 JT_API jt_status jt_plan_info(const jt_plan *plan, jt_plan_info_t *out);

@@ -598,15 +598,17 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   }
   P.tile = 32 * P.cpt_per_thread;
   // Rows per warp item: fixed by the option (rows per block / warps), else
-  // chosen per layer so that a layer has about 192 warp items per case tile,
+  // chosen per layer so that a layer has about items_per_tile (default 192)
+  // warp items per case tile,
   // between 32 rows (one index batch) and 512: a small layer is
   // latency-bound and finishes sooner in short items, a big one amortises
   // each item's set-up over long ones.
   P.rows_per_cta = opts.rows_per_cta > 0 ? opts.rows_per_cta : 0;
   auto layer_rows = [&](int64_t total) -> int64_t {
     if (opts.rows_per_cta > 0) return std::max<int64_t>(1, opts.rows_per_cta / NW);
+    const int64_t items = opts.items_per_tile > 0 ? opts.items_per_tile : 192;
     int64_t r = 32;
-    while (r < 512 && r * 2 * 192 <= total) r *= 2;
+    while (r < 512 && r * 2 * items <= total) r *= 2;
     return r;
   };
   P.citems.clear();

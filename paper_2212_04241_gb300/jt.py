@@ -30,7 +30,8 @@ class CompileOpts(ctypes.Structure):
     _fields_ = [("root_rule", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("cases_per_thread", ctypes.c_int32), ("rows_per_cta", ctypes.c_int32),
                 ("max_clique_entries", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
-                ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("use_graphs", ctypes.c_int32), ("items_per_tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -48,7 +49,7 @@ class PlanInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["jt_default_opts", "jt_compile", "jt_infer", "jt_infer_device", "jt_infer_plain", "jt_profile",
+EXPORTS = ["jt_default_opts", "jt_compile", "jt_autotune", "jt_infer", "jt_infer_device", "jt_infer_plain", "jt_profile",
            "jt_plan_info", "jt_plan_clique", "jt_plan_free", "jt_status_string", "jt_last_error",
            "jt_server_create", "jt_server_add_plan", "jt_submit", "jt_poll", "jt_server_drain",
            "jt_server_stats", "jt_server_destroy"]
@@ -62,6 +63,8 @@ def _load():
     sig = {
         "jt_default_opts": ([ctypes.POINTER(CompileOpts)], None),
         "jt_compile": ([I32, P, P, P, P, ctypes.POINTER(CompileOpts), ctypes.POINTER(P)], ctypes.c_int),
+        "jt_autotune": ([I32, P, P, P, P, ctypes.POINTER(CompileOpts), I32, ctypes.POINTER(CompileOpts),
+                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "jt_infer": ([P, I32, P, P, P, P, P], ctypes.c_int),
         "jt_infer_device": ([P, I32, P, P, P, P, P], ctypes.c_int),
         "jt_infer_plain": ([P, I32, P, P, P, P, P], ctypes.c_int),
@@ -109,6 +112,30 @@ def default_opts(**kw) -> CompileOpts:
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def _net_arrays(net):
+    card = np.ascontiguousarray(net.card, dtype=np.int32)
+    pptr = np.ascontiguousarray(net.parent_ptr, dtype=np.int32)
+    par = np.ascontiguousarray(net.parents, dtype=np.int32)
+    if par.size == 0:
+        par = np.zeros(1, dtype=np.int32)
+    cpt = np.ascontiguousarray(net.cpt, dtype=np.float64)
+    return card, pptr, par, cpt
+
+
+def autotune(net, n_cases: int, **opts):
+    """jt_autotune: the fastest tile shape for this network and batch size.
+    Returns (options dict for Plan(...), ns per case)."""
+    card, pptr, par, cpt = _net_arrays(net)
+    base = default_opts(**opts)
+    best = CompileOpts()
+    ns = ctypes.c_double()
+    _check(lib.jt_autotune(int(net.n), _ptr(card), _ptr(pptr), _ptr(par), _ptr(cpt), ctypes.byref(base),
+                           int(n_cases), ctypes.byref(best), ctypes.byref(ns)))
+    out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
+                                           "use_graphs", "arena_bytes", "max_clique_entries")}
+    return out, ns.value
 
 
 class Plan:

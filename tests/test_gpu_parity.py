@@ -228,3 +228,13 @@ def test_bn420_arena_batch_sampled():
     olp, opost, ost = _oracle(net, ev[idx[:4]])
     np.testing.assert_allclose(plp, olp, atol=1e-10)
     np.testing.assert_allclose(ppost, opost, atol=1e-10)
+
+
+def test_autotuned_plan_parity():
+    net = configs.network("bn60")
+    ev = configs.evidence("bn60", net, n_cases=512)
+    opts, ns = J.autotune(net, 512)
+    assert opts["cases_per_thread"] in (4, 8) and opts["items_per_tile"] in (96, 192, 384)
+    assert ns > 0
+    p = J.Plan(net, **opts)
+    assert_parity32(*p.infer(ev), *_oracle(net, ev), where=f"autotuned {opts}")
