@@ -86,7 +86,7 @@ typedef struct {
                                  JT_EINVAL); used to inspect a plan */
   int32_t cases_per_thread;   /* 1, 2, 4 or 8: each GPU thread carries this
                                  many evidence cases, a case tile is 32x that;
-                                 0 = automatic (8; use 1 for small batches) */
+                                 0 = automatic (4; use 1 for small batches) */
   int32_t rows_per_cta;       /* table rows (entries) per thread block of a
                                  layer launch; 0 = automatic (per plan) */
   int64_t max_clique_entries; /* JT_ETOOBIG above this; 0 = 2^31 - 1 */

@@ -526,7 +526,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       DMap mp{};
       mp.kind = MAP_EVIDENCE;
       mp.src = v;
-      mp.src_row = 0;
+      mp.src_row = P.post_off[v];  // first row of v's indicator table
       mp.A_off = table_or_zero(up_card, wa);
       mp.B_off = table_or_zero(res_card, wb);
       P.dmap.push_back(mp);
@@ -591,7 +591,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   // per-layer thread-block lists
   // ---------------------------------------------------------------------
   const int NW = 8;  // warps per block
-  P.cpt_per_thread = opts.cases_per_thread > 0 ? opts.cases_per_thread : 8;
+  P.cpt_per_thread = opts.cases_per_thread > 0 ? opts.cases_per_thread : 4;
   if (P.cpt_per_thread != 1 && P.cpt_per_thread != 2 && P.cpt_per_thread != 4 && P.cpt_per_thread != 8) {
     err = "cases_per_thread must be 1, 2, 4 or 8";
     return JT_EINVAL;

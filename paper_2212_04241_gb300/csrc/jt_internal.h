@@ -35,12 +35,13 @@ struct DClique {
 
 // A linear index map over a clique's entries: idx(s*R + u) = A[s] + B[u].
 //   kind MAP_CHILD: idx is the entry of child clique `src`'s upward message
-//   kind MAP_EVIDENCE: idx is the state of variable `src` (evidence test)
+//   kind MAP_EVIDENCE: idx is the state of variable `src`; the row of its
+//     evidence indicator table (1, or 0 where the state contradicts the case)
 enum { MAP_CHILD = 0, MAP_EVIDENCE = 1 };
 struct DMap {
   int64_t A_off;      // int32 pool offset, nsep entries
   int64_t B_off;      // int32 pool offset, R entries
-  int64_t src_row;    // MAP_CHILD: child's sep_row
+  int64_t src_row;    // MAP_CHILD: child's sep_row; MAP_EVIDENCE: variable's posterior/indicator row
   int32_t kind;
   int32_t src;        // child clique / variable
 };

@@ -34,6 +34,11 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGroup = 4;  // rows whose loads a warp issues together
+// Resident blocks per SM the register allocation aims at: the collect
+// kernel keeps its row group in registers without spilling at 2; the
+// distribute kernel streams psi and gains from more warps in flight.
+constexpr int kCollectBlocksPerSM = 2;
+constexpr int kDistributeBlocksPerSM = 4;
 
 // CPT cases of one thread inside a row of W = 32*CPT cases.  For CPT >= 4
 // the thread holds CPT/4 float4 pieces, piece v at columns 128*v + 4*lane;
@@ -113,17 +118,73 @@ __device__ __forceinline__ void strow(float *row, int lane, const Vec<CPT> &a) {
   }
 }
 
+// Paired FP32 arithmetic (Blackwell add/sub/mul .rn.f32x2): two cases per
+// instruction, each element rounded exactly like the scalar operation.
+__device__ __forceinline__ void mul2(float &a0, float &a1, float b0, float b1) {
+  asm("{\n .reg .b64 pa, pb;\n mov.b64 pa, {%0, %1};\n mov.b64 pb, {%2, %3};\n"
+      " mul.rn.f32x2 pa, pa, pb;\n mov.b64 {%0, %1}, pa;\n}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void add2(float &a0, float &a1, float b0, float b1) {
+  asm("{\n .reg .b64 pa, pb;\n mov.b64 pa, {%0, %1};\n mov.b64 pb, {%2, %3};\n"
+      " add.rn.f32x2 pa, pa, pb;\n mov.b64 {%0, %1}, pa;\n}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void sub2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+  asm("{\n .reg .b64 pa, pb;\n mov.b64 pa, {%2, %3};\n mov.b64 pb, {%4, %5};\n"
+      " sub.rn.f32x2 pa, pa, pb;\n mov.b64 {%0, %1}, pa;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// a *= b per case
+template <int CPT>
+__device__ __forceinline__ void vmul(Vec<CPT> &a, const Vec<CPT> &b) {
+  if constexpr (CPT >= 2) {
+#pragma unroll
+    for (int k = 0; k < CPT; k += 2) mul2(a.x[k], a.x[k + 1], b.x[k], b.x[k + 1]);
+  } else {
+    a.x[0] *= b.x[0];
+  }
+}
+
+// a += b per case
+template <int CPT>
+__device__ __forceinline__ void vadd(Vec<CPT> &a, const Vec<CPT> &b) {
+  if constexpr (CPT >= 2) {
+#pragma unroll
+    for (int k = 0; k < CPT; k += 2) add2(a.x[k], a.x[k + 1], b.x[k], b.x[k + 1]);
+  } else {
+    a.x[0] += b.x[0];
+  }
+}
+
 // Compensated (Kahan) accumulation per case of a partial sum: long FP32
 // sums keep a few ulp.
 template <int CPT>
 __device__ __forceinline__ void kahan_fold(Vec<CPT> &sum, Vec<CPT> &comp, Vec<CPT> &part) {
+  if constexpr (CPT >= 2) {
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) {
-    const float y = part.x[k] - comp.x[k];
-    const float t = sum.x[k] + y;
-    comp.x[k] = (t - sum.x[k]) - y;
-    sum.x[k] = t;
-    part.x[k] = 0.f;
+    for (int k = 0; k < CPT; k += 2) {
+      float y0, y1, d0, d1;
+      sub2(y0, y1, part.x[k], part.x[k + 1], comp.x[k], comp.x[k + 1]);  // y = part - comp
+      float t0 = sum.x[k], t1 = sum.x[k + 1];
+      add2(t0, t1, y0, y1);                                               // t = sum + y
+      sub2(d0, d1, t0, t1, sum.x[k], sum.x[k + 1]);                       // t - sum
+      sub2(comp.x[k], comp.x[k + 1], d0, d1, y0, y1);                     // comp = (t - sum) - y
+      sum.x[k] = t0;
+      sum.x[k + 1] = t1;
+      part.x[k] = 0.f;
+      part.x[k + 1] = 0.f;
+    }
+  } else {
+    const float y = part.x[0] - comp.x[0];
+    const float t = sum.x[0] + y;
+    comp.x[0] = (t - sum.x[0]) - y;
+    sum.x[0] = t;
+    part.x[0] = 0.f;
   }
 }
 
@@ -159,6 +220,8 @@ __global__ void k_evidence(const int32_t *__restrict__ ev_in, int32_t n_cases, D
       }
     }
     A.ev[((c / W) * P.n_vars + v) * W + (c % W)] = val;
+    float *lam = A.lam + ((c / W) * P.post_rows + P.post_off[v]) * W + (c % W);
+    for (int s = 0; s < P.card[v]; ++s) lam[(int64_t)s * W] = (val < 0 || val == s) ? 1.f : 0.f;
   }
 }
 
@@ -231,7 +294,7 @@ __host__ __device__ inline size_t collect_warp_smem(int cpt, int nm) {
 }
 
 template <int CPT>
-__global__ void __launch_bounds__(kThreads, 2) k_collect(DevPlan P, DevArena A, int64_t item_begin,
+__global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPlan P, DevArena A, int64_t item_begin,
                                                           int64_t n_items, int max_maps) {
   constexpr int W = 32 * CPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,21 +313,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_collect(DevPlan P, DevArena A, 
   int32_t *idx = reinterpret_cast<int32_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps) +
                                              round16(3 * sizeof(int64_t) * (size_t)max_maps));
 
+  // child maps gather rows of the child's message (scaled by 2^-k per case),
+  // evidence maps gather rows of the variable's 0/1 indicator table
   int nchild = 0;
   for (int i = 0; i < nm; ++i) {
     const DMap mp = P.maps[C.map_begin + i];
+    const bool child = mp.kind == MAP_CHILD;
     if (lane == 0) {
       mA[i] = mp.A_off;
       mB[i] = mp.B_off;
-      mrow[i] = ((int64_t)tile * P.sep_rows + mp.src_row) * W;
+      mrow[i] = child ? (A.phistar - A.psi) + ((int64_t)tile * P.sep_rows + mp.src_row) * W
+                      : (A.lam - A.psi) + ((int64_t)tile * P.post_rows + mp.src_row) * W;
     }
-    nchild += (mp.kind == MAP_CHILD);
+    nchild += child;
+    if (child) {
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-      const int c = col_of<CPT>(lane, k);
-      mval[i * W + c] = (mp.kind == MAP_CHILD)
-                            ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]))
-                            : __int_as_float(A.ev[((int64_t)tile * P.n_vars + mp.src) * W + c]);
+      for (int k = 0; k < CPT; ++k) {
+        const int c = col_of<CPT>(lane, k);
+        mval[i * W + c] = pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]));
+      }
     }
   }
   __syncwarp();
@@ -290,35 +357,41 @@ __global__ void __launch_bounds__(kThreads, 2) k_collect(DevPlan P, DevArena A, 
       Vec<CPT> v[kGroup];
 #pragma unroll
       for (int g = 0; g < kGroup; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
-      for (int i = 0; i < nchild; ++i) {
-        const float *mp = A.phistar + mrow[i];
-        Vec<CPT> m[kGroup];
+      // two maps at a time: both maps' rows are requested before either is used
+      for (int i = 0; i < nm; i += 2) {
+        const bool two = i + 1 < nm;
+        const float *mp0 = A.psi + mrow[i];
+        const float *mp1 = A.psi + mrow[two ? i + 1 : i];
+        Vec<CPT> m0[kGroup], m1[kGroup];
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g) m[g] = ldrow<CPT, LD_NC>(mp + (int64_t)idx[i * 32 + min(r + g, nb - 1)] * W, lane);
-        const Vec<CPT> sc = ldrow<CPT>(mval + i * W, lane);
+        for (int g = 0; g < kGroup; ++g) m0[g] = ldrow<CPT, LD_NC>(mp0 + (int64_t)idx[i * 32 + min(r + g, nb - 1)] * W, lane);
+        if (two) {
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g)
+          for (int g = 0; g < kGroup; ++g)
+            m1[g] = ldrow<CPT, LD_NC>(mp1 + (int64_t)idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
+        }
+        if (i < nchild) {
+          const Vec<CPT> sc = ldrow<CPT>(mval + i * W, lane);
 #pragma unroll
-          for (int k = 0; k < CPT; ++k) v[g].x[k] *= m[g].x[k] * sc.x[k];
-      }
-      for (int i = nchild; i < nm; ++i) {
-        int ev[CPT];
+          for (int g = 0; g < kGroup; ++g) vmul<CPT>(m0[g], sc);
+        }
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) ev[k] = __float_as_int(mval[i * W + col_of<CPT>(lane, k)]);
+        for (int g = 0; g < kGroup; ++g) vmul<CPT>(v[g], m0[g]);
+        if (two) {
+          if (i + 1 < nchild) {
+            const Vec<CPT> sc = ldrow<CPT>(mval + (i + 1) * W, lane);
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g) {
-          const int d = idx[i * 32 + min(r + g, nb - 1)];
+            for (int g = 0; g < kGroup; ++g) vmul<CPT>(m1[g], sc);
+          }
 #pragma unroll
-          for (int k = 0; k < CPT; ++k)
-            if (ev[k] >= 0 && ev[k] != d) v[g].x[k] = 0.f;
+          for (int g = 0; g < kGroup; ++g) vmul<CPT>(v[g], m1[g]);
         }
       }
 #pragma unroll
       for (int g = 0; g < kGroup; ++g) {
         if (r + g < nb) {
           strow<CPT, true>(psi + (e_first + b0 + r + g) * W, lane, v[g]);
-#pragma unroll
-          for (int k = 0; k < CPT; ++k) part.x[k] += v[g].x[k];
+          vadd<CPT>(part, v[g]);
           if ((last >> (r + g)) & 1u) {  // segment complete
             kahan_fold<CPT>(acc, comp, part);
             const int32_t s = __shfl_sync(kFull, sj, r + g);
@@ -353,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_collect(DevPlan P, DevArena A, 
 // distribute
 // ---------------------------------------------------------------------------
 template <int CPT>
-__global__ void __launch_bounds__(kThreads, 2) k_distribute(DevPlan P, DevArena A, int64_t item_begin,
+__global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute(DevPlan P, DevArena A, int64_t item_begin,
                                                              int64_t n_items) {
   constexpr int W = 32 * CPT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -414,20 +487,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_distribute(DevPlan P, DevArena 
         for (int g = 0; g < kGroup; ++g)
           q[g] = ldrow<CPT, LD_NC>(rho + (int64_t)__shfl_sync(kFull, xj, min(r + g, nb - 1)) * W, lane);
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g)
-#pragma unroll
-          for (int k = 0; k < CPT; ++k) p[g].x[k] *= q[g].x[k];
+        for (int g = 0; g < kGroup; ++g) vmul<CPT>(p[g], q[g]);
       } else {
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g)
-#pragma unroll
-          for (int k = 0; k < CPT; ++k) p[g].x[k] *= rs.x[k];
+        for (int g = 0; g < kGroup; ++g) vmul<CPT>(p[g], rs);
       }
 #pragma unroll
       for (int g = 0; g < kGroup; ++g) {
         if (r + g < nb) {
-#pragma unroll
-          for (int k = 0; k < CPT; ++k) part.x[k] += p[g].x[k];
+          vadd<CPT>(part, p[g]);
           if ((last >> (r + g)) & 1u) {  // target entry complete
             kahan_fold<CPT>(acc, comp, part);
             output(__shfl_sync(kFull, tj, r + g), acc);
@@ -657,10 +725,7 @@ void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, 
   else k_distribute<1><<<grid, kThreads, 0, s>>>(P, A, b, n);
 }
 
-cudaError_t configure_distribute_smem(int cpt) {
-  (void)cpt;  // the distribute kernel uses static shared memory only
-  return cudaSuccess;
-}
+cudaError_t configure_distribute_smem(int cpt) { (void)cpt; return cudaSuccess; }
 
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,
                        const int32_t *d_ev, cudaStream_t s) {
