@@ -416,7 +416,7 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[name], "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
                    "chunk_cases": info["chunk_cases"], "levels": info["n_levels"],
-                   "autotuned": {k: tuned[k] for k in ("cases_per_thread", "items_per_tile")} if tuned else None,
+                   "autotuned": {k: tuned[k] for k in ("cases_per_thread", "items_per_tile", "items_per_tile_distribute")} if tuned else None,
                    "sum_clique_entries": info["sum_clique_entries"],
                    "l2": "inputs larger than L2 (psi arena %.2f GB per step)" % (4.0 * info["sum_clique_entries"] * n_cases / 1e9),
                    "parallelism": f"cases sharded, {world} rank(s)"},

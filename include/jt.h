@@ -96,10 +96,13 @@ typedef struct {
   int32_t use_graphs;         /* 1 (default): replay the layer launches of a
                                  batch chunk as one captured CUDA graph */
   int32_t items_per_tile;     /* target warp work items per case tile and
-                                 tree layer when rows_per_cta is 0: small
-                                 values give long items, large values short
-                                 ones; 0 = automatic (192) */
-  int32_t reserved[6];
+                                 tree layer of the collect pass when
+                                 rows_per_cta is 0: small values give long
+                                 items, large values short ones;
+                                 0 = automatic (192) */
+  int32_t items_per_tile_distribute; /* the same for the distribute pass;
+                                 0 = items_per_tile */
+  int32_t reserved[5];
 } jt_compile_opts;
 
 typedef struct {
@@ -221,11 +224,13 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
 /*
  * Autotuner (no counterpart in the paper): compiles the network with each
  * candidate tile shape -- cases per thread in {4, 8} and work items per
- * tile and layer in {96, 192, 384} -- times batched inference of n_cases
- * cases on the current device (CUDA events, one warm-up and three timed
- * runs each), and writes the fastest options to *best (base fields kept)
- * and its time per case in ns to *best_ns_per_case (may be NULL).  base may
- * be NULL for the defaults.  Allocates and frees its own device memory.
+ * tile and layer in {96, 192, 384} -- times the collect and the distribute
+ * launches of n_cases cases separately on the current device (CUDA events
+ * around every launch, best of three runs after a warm-up), picks per tile
+ * width the best items value of each pass, and writes the fastest
+ * combination to *best (base fields kept) and its layer-kernel time per
+ * case in ns to *best_ns_per_case (may be NULL).  base may be NULL for the
+ * defaults.  Allocates and frees its own device memory.
  */
 JT_API jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
                              const int32_t *parents, const double *cpt, const jt_compile_opts *base,

@@ -709,68 +709,74 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
 extern "C" jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
                                  const int32_t *parents, const double *cpt, const jt_compile_opts *base,
                                  int32_t n_cases, jt_compile_opts *best, double *best_ns_per_case) {
-  if (!best || n_cases <= 0) { set_error("bad argument"); return JT_EINVAL; }
+  if (!best || n_cases <= 0 || n_vars <= 0 || !card) { set_error("bad argument"); return JT_EINVAL; }
   jt_compile_opts b;
   if (base) b = *base; else jt_default_opts(&b);
   b.host_only = 0;
   const int cpts[] = {4, 8};
   const int items[] = {96, 192, 384};
-  double best_ms = -1;
-  jt_compile_opts best_o = b;
+  int64_t sum_card = 0;
+  for (int v = 0; v < n_vars; ++v) sum_card += card[v];
   int32_t *d_ev = nullptr;
   double *d_lp = nullptr, *d_post = nullptr;
   int32_t *d_st = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  jt_status result = JT_OK;
-  int64_t sum_card = 0;
-  for (int v = 0; v < n_vars; ++v) sum_card += card ? card[v] : 0;
   if (cudaMalloc(&d_ev, sizeof(int32_t) * (size_t)n_cases * n_vars) != cudaSuccess ||
       cudaMalloc(&d_lp, sizeof(double) * n_cases) != cudaSuccess ||
       cudaMalloc(&d_post, sizeof(double) * (size_t)n_cases * sum_card) != cudaSuccess ||
       cudaMalloc(&d_st, sizeof(int32_t) * n_cases) != cudaSuccess) {
     cudaGetLastError();
+    cudaFree(d_ev); cudaFree(d_lp); cudaFree(d_post); cudaFree(d_st);
     set_error("autotune buffers");
-    result = JT_ENOMEM;
+    return JT_ENOMEM;
   }
-  if (result == JT_OK) {
-    // all variables unobserved: timing does not depend on the evidence values
-    cudaMemset(d_ev, 0xff, sizeof(int32_t) * (size_t)n_cases * n_vars);
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-  }
+  // all variables unobserved: the timing does not depend on the evidence values
+  cudaMemset(d_ev, 0xff, sizeof(int32_t) * (size_t)n_cases * n_vars);
+  jt_status result = JT_OK;
+  double best_total = -1;
+  jt_compile_opts best_o = b;
   for (int ci = 0; result == JT_OK && ci < 2; ++ci) {
+    if (base && base->cases_per_thread != 0 && ci > 0) break;  // the caller fixed the tile width
+    const int cw = (base && base->cases_per_thread != 0) ? base->cases_per_thread : cpts[ci];
+    double best_c = -1, best_d = -1;
+    int item_c = 192, item_d = 192;
     for (int ii = 0; result == JT_OK && ii < 3; ++ii) {
       jt_compile_opts o = b;
-      if (!base || base->cases_per_thread == 0) o.cases_per_thread = cpts[ci];
-      else if (ci > 0) continue;  // caller fixed the tile width
+      o.cases_per_thread = cw;
       o.items_per_tile = items[ii];
+      o.items_per_tile_distribute = items[ii];
       o.rows_per_cta = 0;
       jt_plan *pl = nullptr;
       jt_status st = jt_compile(n_vars, card, parent_ptr, parents, cpt, &o, &pl);
       if (st != JT_OK) { result = st; break; }
-      cudaStream_t s = pl->stream;
-      st = jt_infer_device(pl, n_cases, d_ev, d_lp, d_post, d_st, s);
-      float ms = 0;
-      if (st == JT_OK) {
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < 3 && st == JT_OK; ++r) st = jt_infer_device(pl, n_cases, d_ev, d_lp, d_post, d_st, s);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) st = JT_ECUDA;
-        cudaEventElapsedTime(&ms, e0, e1);
+      double c_ms = -1, d_ms = -1, out[6];
+      for (int r = 0; r < 4 && st == JT_OK; ++r) {
+        st = jt_profile(pl, n_cases, d_ev, d_lp, d_post, d_st, pl->stream, out);
+        if (st == JT_OK && r > 0) {  // first run warms up
+          c_ms = (c_ms < 0) ? out[0] : std::min(c_ms, out[0]);
+          d_ms = (d_ms < 0) ? out[1] : std::min(d_ms, out[1]);
+        }
       }
       jt_plan_free(pl);
       if (st != JT_OK) { result = st; break; }
-      if (best_ms < 0 || ms < best_ms) { best_ms = ms; best_o = o; }
+      if (best_c < 0 || c_ms < best_c) { best_c = c_ms; item_c = items[ii]; }
+      if (best_d < 0 || d_ms < best_d) { best_d = d_ms; item_d = items[ii]; }
+    }
+    if (result != JT_OK) break;
+    if (best_total < 0 || best_c + best_d < best_total) {
+      best_total = best_c + best_d;
+      best_o = b;
+      best_o.cases_per_thread = cw;
+      best_o.items_per_tile = item_c;
+      best_o.items_per_tile_distribute = item_d;
+      best_o.rows_per_cta = 0;
     }
   }
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
   cudaFree(d_ev);
   cudaFree(d_lp);
   cudaFree(d_post);
   cudaFree(d_st);
   if (result != JT_OK) return result;
   *best = best_o;
-  if (best_ns_per_case) *best_ns_per_case = best_ms / 3.0 * 1e6 / n_cases;
+  if (best_ns_per_case) *best_ns_per_case = best_total * 1e6 / n_cases;
   return JT_OK;
 }

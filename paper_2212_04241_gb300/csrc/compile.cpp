@@ -604,9 +604,10 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   // latency-bound and finishes sooner in short items, a big one amortises
   // each item's set-up over long ones.
   P.rows_per_cta = opts.rows_per_cta > 0 ? opts.rows_per_cta : 0;
-  auto layer_rows = [&](int64_t total) -> int64_t {
+  auto layer_rows = [&](int64_t total, bool distribute) -> int64_t {
     if (opts.rows_per_cta > 0) return std::max<int64_t>(1, opts.rows_per_cta / NW);
-    const int64_t items = opts.items_per_tile > 0 ? opts.items_per_tile : 192;
+    int64_t items = opts.items_per_tile > 0 ? opts.items_per_tile : 192;
+    if (distribute && opts.items_per_tile_distribute > 0) items = opts.items_per_tile_distribute;
     int64_t r = 32;
     while (r < 512 && r * 2 * items <= total) r *= 2;
     return r;
@@ -672,7 +673,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       crows += P.cl[c].size;
       for (int t : tasks_of[c]) drows += P.dtask[t].T * P.dtask[t].U;
     }
-    const int64_t cR = layer_rows(crows), dR = layer_rows(drows);
+    const int64_t cR = layer_rows(crows, false), dR = layer_rows(drows, true);
     for (int c = 0; c < m; ++c) {
       if (P.cl[c].depth != L) continue;
       emit(P.citems, c, P.cl[c].nsep, P.cl[c].R, cR);

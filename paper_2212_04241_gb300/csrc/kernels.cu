@@ -518,12 +518,17 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
 // ---------------------------------------------------------------------------
 constexpr int kStageCols = 16;
 
+constexpr int kLogpeSlices = 4;  // thread rows of a k_logpe block, each over a share of the components
+
 __global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *__restrict__ log_pe,
                         int32_t *__restrict__ status) {
+  __shared__ double s_lz[kLogpeSlices][256];
+  __shared__ long long s_K[kLogpeSlices][256];
+  __shared__ int s_zero[kLogpeSlices][256];
   const int tile = blockIdx.x;
-  const int c = threadIdx.x;
+  const int c = threadIdx.x;      // case within the tile
+  const int slice = threadIdx.y;  // share of the component roots
   const int64_t cs = (int64_t)tile * W + c;
-  if (cs >= n_cases) return;
   // Messages multiplied into a parent were scaled by 2^-k: add k back.
   // Every component root contributes the log of its total -- except a
   // component without any observed variable, whose probability is exactly 1
@@ -538,11 +543,24 @@ __global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *_
       observed = A.ev[((int64_t)tile * P.n_vars + P.comp_vars[k]) * W + c] >= 0;
     if (!observed) continue;
     const DClique &D = P.cl[cl];
-    const float z = A.phistar[((int64_t)tile * P.sep_rows + D.sep_row) * W + c];
-    if (z > 0.f) lz += log((double)z); else zero = 1;
-    K += D.comp_base_exp;
-    for (int k = D.comp_begin; k < D.comp_end; ++k)
+    if (q % kLogpeSlices == slice) {
+      const float z = A.phistar[((int64_t)tile * P.sep_rows + D.sep_row) * W + c];
+      if (z > 0.f) lz += log((double)z); else zero = 1;
+      K += D.comp_base_exp;
+    }
+    // the component's other cliques, shared among the slices
+    for (int k = D.comp_begin + slice; k < D.comp_end; k += kLogpeSlices)
       K += pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + P.comp_cliques[k]) * W + c]);
+  }
+  s_lz[slice][c] = lz;
+  s_K[slice][c] = K;
+  s_zero[slice][c] = zero;
+  __syncthreads();
+  if (slice != 0 || cs >= n_cases) return;
+  for (int t = 1; t < kLogpeSlices; ++t) {
+    lz += s_lz[t][c];
+    K += s_K[t][c];
+    zero |= s_zero[t][c];
   }
   const int bad = A.bad[cs];
   const int st = bad ? JT_CASE_BAD_EVIDENCE : (zero ? JT_CASE_ZERO_EVIDENCE : JT_CASE_OK);
@@ -755,7 +773,7 @@ void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cas
   if (n_cases <= 0) return;
   const int W = 32 * cpt;
   const unsigned tiles = (unsigned)((n_cases + W - 1) / W);
-  k_logpe<<<tiles, W, 0, s>>>(P, A, W, n_cases, d_log_pe, d_status);
+  k_logpe<<<tiles, dim3(W, kLogpeSlices), 0, s>>>(P, A, W, n_cases, d_log_pe, d_status);
   const size_t smem = sizeof(double) * (size_t)W * (kStageCols + 1);
   k_posterior<<<dim3(tiles, (unsigned)P.n_pgroups), W, smem, s>>>(P, A, W, n_cases, d_status, d_post);
 }

@@ -31,7 +31,7 @@ class CompileOpts(ctypes.Structure):
                 ("cases_per_thread", ctypes.c_int32), ("rows_per_cta", ctypes.c_int32),
                 ("max_clique_entries", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
                 ("use_graphs", ctypes.c_int32), ("items_per_tile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("items_per_tile_distribute", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -134,7 +134,8 @@ def autotune(net, n_cases: int, **opts):
     _check(lib.jt_autotune(int(net.n), _ptr(card), _ptr(pptr), _ptr(par), _ptr(cpt), ctypes.byref(base),
                            int(n_cases), ctypes.byref(best), ctypes.byref(ns)))
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
-                                           "use_graphs", "arena_bytes", "max_clique_entries")}
+                                           "items_per_tile_distribute", "use_graphs", "arena_bytes",
+                                           "max_clique_entries")}
     return out, ns.value
 
 
