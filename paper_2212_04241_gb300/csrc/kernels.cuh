@@ -16,6 +16,8 @@ struct DevPlan {
   const DTask *tasks;
   const DItem *citems;
   const DItem *ditems;
+  const DItem *mitems;
+  const DMulti *multis;
   const int32_t *ipool;
   const float *base32;
   const int32_t *card;       // [n]
@@ -70,7 +72,9 @@ size_t collect_warp_smem_bytes(int cpt, int max_maps);   // one warp
 constexpr size_t kCollectSmemLimit = 220 * 1024;
 // raise the dynamic shared-memory limits of the layer kernels (once per plan)
 cudaError_t configure_collect_smem(int cpt, size_t bytes);
-cudaError_t configure_distribute_smem(int cpt);
+cudaError_t configure_distribute_smem(int cpt, int acc_rows);
+void launch_distribute_multi(int cpt, const DevPlan &P, const DevArena &A, int64_t item_begin, int64_t n_items,
+                             int acc_rows, cudaStream_t s);
 constexpr int kMaxTilesPerChunk = 16384;
 
 // plain FP64 path

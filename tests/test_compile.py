@@ -118,3 +118,9 @@ def test_algorithmic_bytes_formula():
     expect = (8 * info["sum_clique_entries"] + 16 * info["sum_sep_entries"] + 4 * net.n
               + 8 * info["sum_card"] + 8)
     assert info["algorithmic_bytes_per_case"] == expect
+
+
+def test_fused_tasks_counted():
+    net = configs.network("bn60")
+    assert J.Plan(net, host_only=1, fuse_children=1).info()["fused_tasks"] > 0
+    assert J.Plan(net, host_only=1).info()["fused_tasks"] == 0
