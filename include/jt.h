@@ -128,6 +128,11 @@ typedef struct {
   double algorithmic_bytes_per_case; /* 8*sum|C| + 16*sum|S| + 4n + 8*sum(card) + 8 */
   int32_t kernels_per_chunk;    /* kernel launches of one batch chunk */
   int32_t fused_tasks;          /* cliques whose child messages share one pass */
+  int32_t separator_evidence_vars; /* variables whose evidence indicator is
+                                 applied to an upward message (a separator
+                                 smaller than every clique holding them)
+                                 rather than gathered per clique entry */
+  int32_t pad;
 } jt_plan_info_t;
 
 /* Fill opts with the defaults listed above. */

@@ -392,6 +392,8 @@ extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
   }
   o->kernels_per_chunk = k;
   o->fused_tasks = (int32_t)P.dmulti.size();
+  o->separator_evidence_vars = 0;
+  for (const HostClique &C : P.cl) o->separator_evidence_vars += (int32_t)C.ev_sep.size();
   return JT_OK;
 }
 

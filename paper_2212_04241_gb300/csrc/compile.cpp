@@ -407,6 +407,38 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       P.cl[P.post_src[v]].owned.push_back(v);
   }
 
+  // Evidence placement of the batched path.  Hugin enters an observed
+  // variable's 0/1 indicator into one table holding the variable; entering
+  // it into a child's upward message before the parent absorbs it gives the
+  // parent the same product, and the later division by that message stays
+  // exact (the indicator is 0 or 1, the calibrated separator is 0 wherever
+  // it is 0, and 0/0 := 0).  Each variable goes to the smallest such table:
+  // an upward separator (one indicator per message entry, applied when the
+  // entry is written) or a clique (one indicator per clique entry), ties to
+  // the separator and then to the lowest clique id.
+  for (int v = 0; v < n; ++v) {
+    int best = -1;
+    bool best_sep = false;
+    int64_t best_cost = 0;
+    for (int c = 0; c < m; ++c) {
+      const HostClique &C = P.cl[c];
+      if (!bit(cbits[c], v)) continue;
+      const bool in_up = C.parent >= 0 && C.n_up > 0 &&
+                         std::find(C.vars.begin(), C.vars.begin() + C.n_up, v) != C.vars.begin() + C.n_up;
+      if (in_up && (best < 0 || C.nsep < best_cost || (C.nsep == best_cost && !best_sep))) {
+        best = c;
+        best_sep = true;
+        best_cost = C.nsep;
+      }
+      if (best < 0 || C.size < best_cost) {
+        best = c;
+        best_sep = false;
+        best_cost = C.size;
+      }
+    }
+    (best_sep ? P.cl[best].ev_sep : P.cl[best].ev_clique).push_back(v);
+  }
+
   P.sum_cl = P.max_cl = P.sum_sep = 0;
   for (int c = 0; c < m; ++c) {
     P.sum_cl += P.cl[c].size;
@@ -518,8 +550,8 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       mp.B_off = table_or_zero(res_card, wb);
       P.dmap.push_back(mp);
     }
-    // evidence digits of the variables homed here
-    for (int v : C.homed) {
+    // evidence digits of the variables whose indicator this clique gathers
+    for (int v : C.ev_clique) {
       std::vector<int64_t> wa(C.n_up, 0), wb(C.vars.size() - C.n_up, 0);
       int pos = (int)(std::find(C.vars.begin(), C.vars.end(), v) - C.vars.begin());
       if (pos < C.n_up) wa[pos] = 1; else wb[pos - C.n_up] = 1;
@@ -532,6 +564,21 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       P.dmap.push_back(mp);
     }
     D.map_end = (int32_t)P.dmap.size();
+    // evidence applied to the upward message: state of v per message entry
+    D.sev_begin = D.map_end;
+    for (int v : C.ev_sep) {
+      std::vector<int64_t> wa(C.n_up, 0);
+      const int pos = (int)(std::find(C.vars.begin(), C.vars.begin() + C.n_up, v) - C.vars.begin());
+      wa[pos] = 1;
+      DMap mp{};
+      mp.kind = MAP_SEP_EVIDENCE;
+      mp.src = v;
+      mp.src_row = P.post_off[v];
+      mp.A_off = table_or_zero(up_card, wa);
+      mp.B_off = 0;
+      P.dmap.push_back(mp);
+    }
+    D.sev_end = (int32_t)P.dmap.size();
   }
   P.cpt_per_thread = opts.cases_per_thread > 0 ? opts.cases_per_thread : 4;
   if (P.cpt_per_thread != 1 && P.cpt_per_thread != 2 && P.cpt_per_thread != 4 && P.cpt_per_thread != 8) {

@@ -30,6 +30,8 @@ struct DClique {
   int32_t comp_begin; // component roots: the other cliques of the component,
   int32_t comp_end;   //   [comp_begin, comp_end) in the comp_cliques list
   int32_t comp_base_exp;  // component roots: sum of the component's base-table exponents
+  int32_t sev_begin;  // evidence applied to its upward message as it is
+  int32_t sev_end;    //   written: MAP_SEP_EVIDENCE maps [sev_begin, sev_end)
   int32_t pad;
 };
 
@@ -37,7 +39,10 @@ struct DClique {
 //   kind MAP_CHILD: idx is the entry of child clique `src`'s upward message
 //   kind MAP_EVIDENCE: idx is the state of variable `src`; the row of its
 //     evidence indicator table (1, or 0 where the state contradicts the case)
-enum { MAP_CHILD = 0, MAP_EVIDENCE = 1 };
+//   kind MAP_SEP_EVIDENCE: the same over the entries s of the clique's
+//     upward message only (A[s] is the state, B unused): the indicator
+//     multiplies the message entry when it is written
+enum { MAP_CHILD = 0, MAP_EVIDENCE = 1, MAP_SEP_EVIDENCE = 2 };
 struct DMap {
   int64_t A_off;      // int32 pool offset, nsep entries
   int64_t B_off;      // int32 pool offset, R entries
@@ -132,7 +137,9 @@ struct HostClique {
   int64_t nsep = 1, R = 1;
   int parent = -1, depth = 0;
   std::vector<int> children;
-  std::vector<int> homed;       // variables whose evidence this clique applies
+  std::vector<int> homed;       // variables whose CPT this clique holds
+  std::vector<int> ev_clique;   // batched path: evidence gathered per clique entry
+  std::vector<int> ev_sep;      // batched path: evidence applied to the upward message
   std::vector<int> owned;       // variables whose posterior this clique's table provides
   std::vector<int> owned_sep;   // variables whose posterior its upward separator provides
 };

@@ -12,9 +12,10 @@
 // time, one row per lane, and broadcast; rows are loaded four at a time.
 //
 //   collect (Section 2: reduction + extension + marginalisation, fused):
-//     psi_C[e] = base_C[e] * [evidence of homed variables] *
+//     psi_C[e] = base_C[e] * [evidence entered in C] *
 //                prod_children phi*_child[map(e)] * 2^-k_child
-//     phi*_C[s] = sum_u psi_C[s*R + u]          (upward separator outermost)
+//     phi*_C[s] = [evidence entered in S_up] * sum_u psi_C[s*R + u]
+//                                              (upward separator outermost)
 //     k_C = exponent of max_s phi*_C[s]          (power-of-two rescaling)
 //   distribute (Hugin: extension by the separator ratio + marginalisation):
 //     for every child separator and owned posterior variable T of C,
@@ -33,7 +34,13 @@ namespace jt {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kGroup = 4;  // rows whose loads a warp issues together
+constexpr int kGroup = 4;  // rows whose loads a warp issues together (fused tasks)
+// The same for the layer kernels, by cases per thread: a group holds
+// 16 cases per lane at most, so wider tiles load fewer rows at once.
+template <int CPT>
+constexpr int kCollectGroup = CPT >= 8 ? 2 : 4;
+template <int CPT>
+constexpr int kDistGroup = CPT >= 8 ? 2 : 4;
 // Resident blocks per SM the register allocation aims at: the collect
 // kernel keeps its row group in registers without spilling at 2; the
 // distribute kernel streams psi and gains from more warps in flight.
@@ -297,6 +304,7 @@ template <int CPT>
 __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPlan P, DevArena A, int64_t item_begin,
                                                           int64_t n_items, int max_maps) {
   constexpr int W = 32 * CPT;
+  constexpr int G = kCollectGroup<CPT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -340,6 +348,16 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
   float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
   float *phi_out = A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
 
+  // evidence entered into the upward message: entry s is multiplied by the
+  // indicator rows of the variables' states at s before it is stored
+  auto sep_evidence = [&](int64_t s, Vec<CPT> &val) {
+    for (int i = C.sev_begin; i < C.sev_end; ++i) {
+      const DMap mp = P.maps[i];
+      const int32_t d = __ldg(P.ipool + mp.A_off + s);
+      vmul<CPT>(val, ldrow<CPT, LD_NC>(A.lam + ((int64_t)tile * P.post_rows + mp.src_row + d) * W, lane));
+    }
+  };
+
   int32_t s_first, u_first, count;
   item_rows(it, R, s_first, u_first, count);
   const int64_t e_first = (int64_t)s_first * R + u_first;  // rows are entries e_first + [0, count)
@@ -348,53 +366,54 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
     const int nb = min(32, count - b0);
     // lane j: indices of row b0 + j
     const int64_t ej = e_first + b0 + min(lane, nb - 1);
-    const int32_t sj = (int32_t)(ej / R), uj = (int32_t)(ej - (int64_t)sj * R);
+    const int32_t sj = (int32_t)ej / R, uj = (int32_t)ej - sj * R;  // |C| < 2^31
     const float bj = __ldg(base + ej);
     for (int i = 0; i < nm; ++i) idx[i * 32 + lane] = __ldg(P.ipool + mA[i] + sj) + __ldg(P.ipool + mB[i] + uj);
     const unsigned last = __ballot_sync(kFull, !it.split && uj == R - 1 && lane < nb);
     __syncwarp();
-    for (int r = 0; r < nb; r += kGroup) {
-      Vec<CPT> v[kGroup];
+    for (int r = 0; r < nb; r += G) {
+      Vec<CPT> v[G];
 #pragma unroll
-      for (int g = 0; g < kGroup; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
+      for (int g = 0; g < G; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
       // two maps at a time: both maps' rows are requested before either is used
       for (int i = 0; i < nm; i += 2) {
         const bool two = i + 1 < nm;
         const float *mp0 = A.psi + mrow[i];
         const float *mp1 = A.psi + mrow[two ? i + 1 : i];
-        Vec<CPT> m0[kGroup], m1[kGroup];
+        Vec<CPT> m0[G], m1[G];
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g) m0[g] = ldrow<CPT, LD_NC>(mp0 + (int64_t)idx[i * 32 + min(r + g, nb - 1)] * W, lane);
+        for (int g = 0; g < G; ++g) m0[g] = ldrow<CPT, LD_NC>(mp0 + (int64_t)idx[i * 32 + min(r + g, nb - 1)] * W, lane);
         if (two) {
 #pragma unroll
-          for (int g = 0; g < kGroup; ++g)
+          for (int g = 0; g < G; ++g)
             m1[g] = ldrow<CPT, LD_NC>(mp1 + (int64_t)idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
         }
         if (i < nchild) {
           const Vec<CPT> sc = ldrow<CPT>(mval + i * W, lane);
 #pragma unroll
-          for (int g = 0; g < kGroup; ++g) vmul<CPT>(m0[g], sc);
+          for (int g = 0; g < G; ++g) vmul<CPT>(m0[g], sc);
         }
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g) vmul<CPT>(v[g], m0[g]);
+        for (int g = 0; g < G; ++g) vmul<CPT>(v[g], m0[g]);
         if (two) {
           if (i + 1 < nchild) {
             const Vec<CPT> sc = ldrow<CPT>(mval + (i + 1) * W, lane);
 #pragma unroll
-            for (int g = 0; g < kGroup; ++g) vmul<CPT>(m1[g], sc);
+            for (int g = 0; g < G; ++g) vmul<CPT>(m1[g], sc);
           }
 #pragma unroll
-          for (int g = 0; g < kGroup; ++g) vmul<CPT>(v[g], m1[g]);
+          for (int g = 0; g < G; ++g) vmul<CPT>(v[g], m1[g]);
         }
       }
 #pragma unroll
-      for (int g = 0; g < kGroup; ++g) {
+      for (int g = 0; g < G; ++g) {
         if (r + g < nb) {
           strow<CPT, true>(psi + (e_first + b0 + r + g) * W, lane, v[g]);
           vadd<CPT>(part, v[g]);
           if ((last >> (r + g)) & 1u) {  // segment complete
             kahan_fold<CPT>(acc, comp, part);
             const int32_t s = __shfl_sync(kFull, sj, r + g);
+            sep_evidence(s, acc);
             strow<CPT>(phi_out + (int64_t)s * W, lane, acc);
 #pragma unroll
             for (int k = 0; k < CPT; ++k) mx.x[k] = fmaxf(mx.x[k], acc.x[k]);
@@ -410,6 +429,7 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
   if (it.split) {
     Vec<CPT> tot;
     if (combine_split<CPT>(it, P, A, tile, lane, acc, tot)) {
+      sep_evidence(it.t0, tot);
       strow<CPT>(phi_out + it.t0 * W, lane, tot);
 #pragma unroll
       for (int k = 0; k < CPT; ++k) mx.x[k] = fmaxf(mx.x[k], tot.x[k]);
@@ -429,6 +449,7 @@ template <int CPT>
 __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute(DevPlan P, DevArena A, int64_t item_begin,
                                                              int64_t n_items) {
   constexpr int W = 32 * CPT;
+  constexpr int G = kDistGroup<CPT>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (iw >= n_items) return;
@@ -476,24 +497,24 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
     const int32_t ej = __ldg(At + tj) + __ldg(Bt + uj);
     const int32_t xj = root ? 0 : __ldg(sAt + tj) + __ldg(sBt + uj);
     const unsigned last = __ballot_sync(kFull, !it.split && uj == U - 1 && lane < nb);
-    for (int r = 0; r < nb; r += kGroup) {
-      Vec<CPT> p[kGroup];
+    for (int r = 0; r < nb; r += G) {
+      Vec<CPT> p[G];
 #pragma unroll
-      for (int g = 0; g < kGroup; ++g)
+      for (int g = 0; g < G; ++g)
         p[g] = ldrow<CPT, LD_STREAM>(psi + (int64_t)__shfl_sync(kFull, ej, min(r + g, nb - 1)) * W, lane);
       if (!root) {
-        Vec<CPT> q[kGroup];
+        Vec<CPT> q[G];
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g)
+        for (int g = 0; g < G; ++g)
           q[g] = ldrow<CPT, LD_NC>(rho + (int64_t)__shfl_sync(kFull, xj, min(r + g, nb - 1)) * W, lane);
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g) vmul<CPT>(p[g], q[g]);
+        for (int g = 0; g < G; ++g) vmul<CPT>(p[g], q[g]);
       } else {
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g) vmul<CPT>(p[g], rs);
+        for (int g = 0; g < G; ++g) vmul<CPT>(p[g], rs);
       }
 #pragma unroll
-      for (int g = 0; g < kGroup; ++g) {
+      for (int g = 0; g < G; ++g) {
         if (r + g < nb) {
           vadd<CPT>(part, p[g]);
           if ((last >> (r + g)) & 1u) {  // target entry complete

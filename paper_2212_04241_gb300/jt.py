@@ -44,7 +44,8 @@ class PlanInfo(ctypes.Structure):
                 ("arena_bytes", ctypes.c_int64), ("static_device_bytes", ctypes.c_int64),
                 ("collect_items", ctypes.c_int64), ("distribute_items", ctypes.c_int64),
                 ("algorithmic_bytes_per_case", ctypes.c_double),
-                ("kernels_per_chunk", ctypes.c_int32), ("fused_tasks", ctypes.c_int32)]
+                ("kernels_per_chunk", ctypes.c_int32), ("fused_tasks", ctypes.c_int32),
+                ("separator_evidence_vars", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -124,3 +124,30 @@ def test_fused_tasks_counted():
     net = configs.network("bn60")
     assert J.Plan(net, host_only=1, fuse_children=1).info()["fused_tasks"] > 0
     assert J.Plan(net, host_only=1).info()["fused_tasks"] == 0
+
+
+@pytest.mark.parametrize("name", ["bn20", "bn60", "bn110", "bn420", "bn1000"])
+def test_evidence_placement_smallest_table(name):
+    """Each variable's evidence indicator enters the smallest table holding
+    it; an upward separator wins ties (Hugin enters evidence into one table;
+    multiplying a child's message by the indicator before the parent absorbs
+    it is the same product).  Recount the separator placements from the
+    plan's cliques."""
+    net = configs.network(name)
+    p = _plan(net)
+    cl, info = _structure(p)
+    size = lambda vs: int(np.prod([net.card[v] for v in vs])) if vs else 1
+    expect = 0
+    for v in range(net.n):
+        best = None  # (cost, is_sep)
+        for vars_, par, _ in cl:
+            if v not in vars_:
+                continue
+            up = [x for x in vars_ if par >= 0 and x in cl[par][0]]
+            if v in up and (best is None or size(up) < best[0] or (size(up) == best[0] and not best[1])):
+                best = (size(up), True)
+            if best is None or size(vars_) < best[0]:
+                best = (size(vars_), False)
+        expect += best[1]
+    assert info["separator_evidence_vars"] == expect
+    assert expect > 0
