@@ -41,7 +41,7 @@ ArenaLayout arena_layout(const Plan &P) {
   L.counters = align_up(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, P.n_groups));
   L.ev = align_up(sizeof(int32_t) * W * (size_t)P.n);
   L.bad = align_up(sizeof(int32_t) * W);
-  L.per_tile = L.psi + 2 * L.sep + 2 * L.post + L.partial + L.maxbits + L.counters + L.ev + L.bad;
+  L.per_tile = L.psi + 2 * L.sep + L.post + L.partial + L.maxbits + L.counters + L.ev + L.bad;
   return L;
 }
 
@@ -66,7 +66,6 @@ static void arena_bind(const Plan &P, Arena &a, char *mem, int tiles) {
   a.da.phistar = reinterpret_cast<float *>(take(L.sep));
   a.da.rho = reinterpret_cast<float *>(take(L.sep));
   a.da.post = reinterpret_cast<float *>(take(L.post));
-  a.da.lam = reinterpret_cast<float *>(take(L.post));
   a.da.partial = reinterpret_cast<float *>(take(L.partial));
   a.da.maxbits = reinterpret_cast<uint32_t *>(take(L.maxbits));
   a.da.counters = reinterpret_cast<uint32_t *>(take(L.counters));

@@ -851,7 +851,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     for (int c = 0; c < m; ++c) {
       if (P.cl[c].depth != L) continue;
       emit(P.citems, c, P.cl[c].nsep, P.cl[c].R, cR);
-      lv.c_max_maps = std::max(lv.c_max_maps, P.dcl[c].map_end - P.dcl[c].map_begin);
+      lv.c_max_maps = std::max(lv.c_max_maps, P.dcl[c].sev_end - P.dcl[c].map_begin);
     }
     lv.c_item_end = (int64_t)P.citems.size();
     lv.d_item_begin = (int64_t)P.ditems.size();

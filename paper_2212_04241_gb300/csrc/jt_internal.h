@@ -37,16 +37,16 @@ struct DClique {
 
 // A linear index map over a clique's entries: idx(s*R + u) = A[s] + B[u].
 //   kind MAP_CHILD: idx is the entry of child clique `src`'s upward message
-//   kind MAP_EVIDENCE: idx is the state of variable `src`; the row of its
-//     evidence indicator table (1, or 0 where the state contradicts the case)
+//   kind MAP_EVIDENCE: idx is the digit (state) of variable `src` at the
+//     entry; the entry is zeroed for the cases that observed another state
 //   kind MAP_SEP_EVIDENCE: the same over the entries s of the clique's
-//     upward message only (A[s] is the state, B unused): the indicator
-//     multiplies the message entry when it is written
+//     upward message only (A[s] is the digit, B unused), applied to the
+//     message entry when it is written
 enum { MAP_CHILD = 0, MAP_EVIDENCE = 1, MAP_SEP_EVIDENCE = 2 };
 struct DMap {
   int64_t A_off;      // int32 pool offset, nsep entries
   int64_t B_off;      // int32 pool offset, R entries
-  int64_t src_row;    // MAP_CHILD: child's sep_row; MAP_EVIDENCE: variable's posterior/indicator row
+  int64_t src_row;    // MAP_CHILD: child's sep_row; evidence maps: the variable's posterior row
   int32_t kind;
   int32_t src;        // child clique / variable
 };

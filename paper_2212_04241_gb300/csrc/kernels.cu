@@ -227,8 +227,6 @@ __global__ void k_evidence(const int32_t *__restrict__ ev_in, int32_t n_cases, D
       }
     }
     A.ev[((c / W) * P.n_vars + v) * W + (c % W)] = val;
-    float *lam = A.lam + ((c / W) * P.post_rows + P.post_off[v]) * W + (c % W);
-    for (int s = 0; s < P.card[v]; ++s) lam[(int64_t)s * W] = (val < 0 || val == s) ? 1.f : 0.f;
   }
 }
 
@@ -290,9 +288,11 @@ __device__ __forceinline__ bool combine_split(const DItem &it, const DevPlan &P,
 // collect
 // ---------------------------------------------------------------------------
 
-// Shared memory of one warp: per map its per-case scale or evidence (read
-// as float4, so it comes first and every part is rounded to 16 bytes), its
-// index-table offsets and message row, and the map indices of 32 rows.
+// Shared memory of one warp: per map (child and evidence maps, then the
+// evidence of the upward message) its per-case value -- the child message's
+// scale 2^-k, or the observed state (-1 if unobserved) -- read as float4, so
+// it comes first and every part is rounded to 16 bytes; its index-table
+// offsets and message row; and the map indices of 32 rows.
 __host__ __device__ inline size_t round16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ inline size_t collect_warp_smem(int cpt, int nm) {
   const int W = 32 * cpt;
@@ -321,25 +321,26 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
   int32_t *idx = reinterpret_cast<int32_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps) +
                                              round16(3 * sizeof(int64_t) * (size_t)max_maps));
 
-  // child maps gather rows of the child's message (scaled by 2^-k per case),
-  // evidence maps gather rows of the variable's 0/1 indicator table
+  // Child maps gather rows of the child's message (scaled by 2^-k per case).
+  // Evidence maps keep each case's observed state: an entry whose digit of
+  // the variable differs from it is zeroed (the 0/1 indicator of the
+  // reduction step, evaluated instead of loaded).  Child maps come first.
+  const int nsev = C.sev_end - C.sev_begin;
   int nchild = 0;
-  for (int i = 0; i < nm; ++i) {
-    const DMap mp = P.maps[C.map_begin + i];
+  for (int i = 0; i < nm + nsev; ++i) {
+    const DMap mp = P.maps[C.map_begin + i];  // the upward message's evidence follows the maps
     const bool child = mp.kind == MAP_CHILD;
     if (lane == 0) {
       mA[i] = mp.A_off;
       mB[i] = mp.B_off;
-      mrow[i] = child ? (A.phistar - A.psi) + ((int64_t)tile * P.sep_rows + mp.src_row) * W
-                      : (A.lam - A.psi) + ((int64_t)tile * P.post_rows + mp.src_row) * W;
+      mrow[i] = child ? (A.phistar - A.psi) + ((int64_t)tile * P.sep_rows + mp.src_row) * W : 0;
     }
     nchild += child;
-    if (child) {
 #pragma unroll
-      for (int k = 0; k < CPT; ++k) {
-        const int c = col_of<CPT>(lane, k);
-        mval[i * W + c] = pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]));
-      }
+    for (int k = 0; k < CPT; ++k) {
+      const int c = col_of<CPT>(lane, k);
+      mval[i * W + c] = child ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]))
+                              : (float)A.ev[((int64_t)tile * P.n_vars + mp.src) * W + c];
     }
   }
   __syncwarp();
@@ -348,13 +349,14 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
   float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
   float *phi_out = A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
 
-  // evidence entered into the upward message: entry s is multiplied by the
-  // indicator rows of the variables' states at s before it is stored
+  // evidence entered into the upward message: entry s is zeroed for the
+  // cases whose observed state of the variable differs from its digit at s
   auto sep_evidence = [&](int64_t s, Vec<CPT> &val) {
-    for (int i = C.sev_begin; i < C.sev_end; ++i) {
-      const DMap mp = P.maps[i];
-      const int32_t d = __ldg(P.ipool + mp.A_off + s);
-      vmul<CPT>(val, ldrow<CPT, LD_NC>(A.lam + ((int64_t)tile * P.post_rows + mp.src_row + d) * W, lane));
+    for (int j = nm; j < nm + nsev; ++j) {
+      const float d = (float)__ldg(P.ipool + mA[j] + s);
+      const Vec<CPT> e = ldrow<CPT>(mval + j * W, lane);
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) val.x[k] = (e.x[k] < 0.f || e.x[k] == d) ? val.x[k] : 0.f;
     }
   };
 
@@ -375,9 +377,9 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
       Vec<CPT> v[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
-      // two maps at a time: both maps' rows are requested before either is used
-      for (int i = 0; i < nm; i += 2) {
-        const bool two = i + 1 < nm;
+      // child maps two at a time: both rows are requested before either is used
+      for (int i = 0; i < nchild; i += 2) {
+        const bool two = i + 1 < nchild;
         const float *mp0 = A.psi + mrow[i];
         const float *mp1 = A.psi + mrow[two ? i + 1 : i];
         Vec<CPT> m0[G], m1[G];
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
           for (int g = 0; g < G; ++g)
             m1[g] = ldrow<CPT, LD_NC>(mp1 + (int64_t)idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
         }
-        if (i < nchild) {
+        {
           const Vec<CPT> sc = ldrow<CPT>(mval + i * W, lane);
 #pragma unroll
           for (int g = 0; g < G; ++g) vmul<CPT>(m0[g], sc);
@@ -396,13 +398,22 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
 #pragma unroll
         for (int g = 0; g < G; ++g) vmul<CPT>(v[g], m0[g]);
         if (two) {
-          if (i + 1 < nchild) {
+          {
             const Vec<CPT> sc = ldrow<CPT>(mval + (i + 1) * W, lane);
 #pragma unroll
             for (int g = 0; g < G; ++g) vmul<CPT>(m1[g], sc);
           }
 #pragma unroll
           for (int g = 0; g < G; ++g) vmul<CPT>(v[g], m1[g]);
+        }
+      }
+      for (int i = nchild; i < nm; ++i) {  // evidence maps: idx is the variable's digit
+        const Vec<CPT> e = ldrow<CPT>(mval + i * W, lane);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const float d = (float)idx[i * 32 + min(r + g, nb - 1)];
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) v[g].x[k] = (e.x[k] < 0.f || e.x[k] == d) ? v[g].x[k] : 0.f;
         }
       }
 #pragma unroll

@@ -47,7 +47,6 @@ struct DevArena {
   float *phistar;      // collect messages (raw sums), one block of rows per clique
   float *rho;          // distribute ratios phi** / phi*, same layout as phistar
   float *post;         // unnormalised posterior marginals
-  float *lam;          // evidence indicators, same rows as post: 1 unless the state contradicts the case
   float *partial;      // partial sums of split segments [tile][slot][W]
   uint32_t *maxbits;   // [tile][clique][W] bit pattern of max psi (>= 0)
   uint32_t *counters;  // [tile][group] pieces finished
