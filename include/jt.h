@@ -102,12 +102,7 @@ typedef struct {
                                  0 = automatic (192) */
   int32_t items_per_tile_distribute; /* the same for the distribute pass;
                                  0 = items_per_tile */
-  int32_t fuse_children;      /* 1: compute the messages to several children
-                                 of a clique in one pass over its table when
-                                 their separators allow it (fewer bytes, but
-                                 slower than separate passes on the tested
-                                 workloads); 0 (default): one pass per child */
-  int32_t reserved[4];
+  int32_t reserved[5];
 } jt_compile_opts;
 
 typedef struct {
@@ -127,12 +122,10 @@ typedef struct {
   int64_t distribute_items;     /* thread blocks per tile, all distribute layers */
   double algorithmic_bytes_per_case; /* 8*sum|C| + 16*sum|S| + 4n + 8*sum(card) + 8 */
   int32_t kernels_per_chunk;    /* kernel launches of one batch chunk */
-  int32_t fused_tasks;          /* cliques whose child messages share one pass */
   int32_t separator_evidence_vars; /* variables whose evidence indicator is
                                  applied to an upward message (a separator
                                  smaller than every clique holding them)
-                                 rather than gathered per clique entry */
-  int32_t pad;
+                                 rather than evaluated per clique entry */
 } jt_plan_info_t;
 
 /* Fill opts with the defaults listed above. */

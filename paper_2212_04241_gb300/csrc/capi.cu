@@ -119,8 +119,6 @@ void enqueue_distribute_layer(const jt_plan *pl, const DevArena &A, int L, cudaS
   const Plan &P = pl->P;
   const Level &lv = P.levels[L];
   launch_distribute(P.cpt_per_thread, pl->dp, A, lv.d_item_begin, lv.d_item_end - lv.d_item_begin, s);
-  launch_distribute_multi(P.cpt_per_thread, pl->dp, A, lv.m_item_begin, lv.m_item_end - lv.m_item_begin,
-                          lv.m_max_acc, s);
 }
 
 // Enqueue the layer launches of one chunk: collect deepest layer first,
@@ -249,7 +247,6 @@ static jt_status upload_plan(jt_plan *pl) {
   std::vector<int32_t> card32(P.card.begin(), P.card.end());
   const size_t o_cl = put(blob, P.dcl), o_map = put(blob, P.dmap), o_task = put(blob, P.dtask);
   const size_t o_ci = put(blob, P.citems), o_di = put(blob, P.ditems), o_ip = put(blob, P.ipool);
-  const size_t o_mi = put(blob, P.mitems), o_mu = put(blob, P.dmulti);
   const size_t o_b32 = put(blob, P.base32), o_card = put(blob, card32), o_po = put(blob, P.post_off);
   const size_t o_cp = put(blob, P.comp_ptr), o_cv = put(blob, P.comp_vars), o_cc = put(blob, P.comp_cliques);
   const size_t o_cr = put(blob, P.comp_roots), o_pg = put(blob, P.pgroup_ptr);
@@ -263,8 +260,6 @@ static jt_status upload_plan(jt_plan *pl) {
   D.tasks = reinterpret_cast<const DTask *>(b + o_task);
   D.citems = reinterpret_cast<const DItem *>(b + o_ci);
   D.ditems = reinterpret_cast<const DItem *>(b + o_di);
-  D.mitems = reinterpret_cast<const DItem *>(b + o_mi);
-  D.multis = reinterpret_cast<const DMulti *>(b + o_mu);
   D.ipool = reinterpret_cast<const int32_t *>(b + o_ip);
   D.base32 = reinterpret_cast<const float *>(b + o_b32);
   D.card = reinterpret_cast<const int32_t *>(b + o_card);
@@ -292,7 +287,6 @@ static jt_status upload_plan(jt_plan *pl) {
     return JT_ETOOBIG;
   }
   JT_CUDA_TRY(configure_collect_smem(P.cpt_per_thread, smem));
-  JT_CUDA_TRY(configure_distribute_smem(P.cpt_per_thread, P.max_acc_rows));
   return JT_OK;
 }
 
@@ -387,10 +381,8 @@ extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
   for (const Level &lv : P.levels) {
     k += lv.c_item_end > lv.c_item_begin;
     k += lv.d_item_end > lv.d_item_begin;
-    k += lv.m_item_end > lv.m_item_begin;
   }
   o->kernels_per_chunk = k;
-  o->fused_tasks = (int32_t)P.dmulti.size();
   o->separator_evidence_vars = 0;
   for (const HostClique &C : P.cl) o->separator_evidence_vars += (int32_t)C.ev_sep.size();
   return JT_OK;
@@ -687,7 +679,7 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
     }
     for (int L = 0; L <= P.height; ++L) {
       const Level &lv = P.levels[L];
-      if (lv.d_item_end == lv.d_item_begin && lv.m_item_end == lv.m_item_begin) continue;
+      if (lv.d_item_end == lv.d_item_begin) continue;
       int a = mark();
       enqueue_distribute_layer(pl, A, L, s);
       spans.push_back({a, mark(), 1});

@@ -586,15 +586,8 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     return JT_EINVAL;
   }
   P.tile = 32 * P.cpt_per_thread;
-  // accumulator rows of a fused task: four blocks of 8 warps per SM keep
-  // their tile-wide accumulator rows within 200 KB of shared memory
-  const int acc_cap = (int)std::min<int64_t>(kMaxAccRows, (200 * 1024) / (4 * 8 * 4 * (int64_t)P.tile));
-
   // distribute tasks: children first (ascending), then owned posteriors
   std::vector<std::vector<int>> tasks_of(m);
-  std::vector<int> multi_of(m, -1);
-  P.dmulti.clear();
-  P.max_acc_rows = 0;
   for (int c = 0; c < m; ++c) {
     const HostClique &C = P.cl[c];
     auto make_task = [&](const std::vector<int> &target, int kind, int dst, int64_t dst_row, bool from_sep = false) {
@@ -637,127 +630,9 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       tasks_of[c].push_back((int)P.dtask.size());
       P.dtask.push_back(t);
     };
-    // children with a non-empty separator; fuse several into one pass when
-    // they share exactly F with the largest separator (see DMulti)
-    std::vector<int> kids;
-    for (int ch : C.children)
-      if (P.cl[ch].n_up > 0) kids.push_back(ch);
-    std::vector<int> fused;  // primary first
-    if (kids.size() >= 2 && opts.fuse_children > 0) {
-      auto sep_vars = [&](int ch) {
-        const HostClique &K = P.cl[ch];
-        return std::vector<int>(K.vars.begin(), K.vars.begin() + K.n_up);
-      };
-      std::vector<int> order = kids;
-      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.cl[a].nsep > P.cl[b].nsep; });
-      const int prim = order[0];
-      const std::vector<int> S1 = sep_vars(prim);
-      auto inter = [&](const std::vector<int> &a) {
-        std::vector<int> r;
-        for (int v : C.vars)  // in the clique's layout order
-          if (std::find(S1.begin(), S1.end(), v) != S1.end() && std::find(a.begin(), a.end(), v) != a.end())
-            r.push_back(v);
-        return r;
-      };
-      const std::vector<int> F = inter(sep_vars(order[1]));
-      std::vector<int> secs;
-      int acc = 0;
-      for (size_t j = 1; j < order.size() && (int)secs.size() < kMaxSec; ++j) {
-        const std::vector<int> Sj = sep_vars(order[j]);
-        if (inter(Sj) != F) continue;
-        int64_t nl = 1;
-        for (int v : Sj)
-          if (std::find(F.begin(), F.end(), v) == F.end()) nl *= card[v];
-        if (acc + nl > acc_cap) continue;
-        acc += (int)nl;
-        secs.push_back(order[j]);
-      }
-      int64_t nF = 1;
-      for (int v : F) nF *= card[v];
-      const int64_t block = C.size / nF;
-      if (!secs.empty() && block <= 65536 && (nF >= 16 || C.size <= 4096)) {
-        fused.push_back(prim);
-        fused.insert(fused.end(), secs.begin(), secs.end());
-        // tables over F, X = S1 \ F and U = C \ S1, all in the clique's layout order
-        std::vector<int> Fv, Xv, Uv;
-        for (int i = 0; i < (int)C.vars.size(); ++i) {
-          const int v = C.vars[i];
-          const bool inS1 = std::find(S1.begin(), S1.end(), v) != S1.end();
-          const bool inF = std::find(F.begin(), F.end(), v) != F.end();
-          (inF ? Fv : inS1 ? Xv : Uv).push_back(i);
-        }
-        // enumerate U with the secondaries' own variables outermost, so that a
-        // secondary entry stays the same over long runs of consecutive rows
-        {
-          std::vector<int> ord;
-          for (int ch : secs) {
-            const std::vector<int> Sj = sep_vars(ch);
-            for (int i : Uv)
-              if (std::find(Sj.begin(), Sj.end(), C.vars[i]) != Sj.end() &&
-                  std::find(ord.begin(), ord.end(), i) == ord.end())
-                ord.push_back(i);
-          }
-          for (int i : Uv)
-            if (std::find(ord.begin(), ord.end(), i) == ord.end()) ord.push_back(i);
-          Uv = ord;
-        }
-        auto tab = [&](const std::vector<int> &pos, auto weight) {
-          std::vector<int> cards;
-          std::vector<int64_t> w;
-          for (int i : pos) { cards.push_back(C.card[i]); w.push_back(weight(i)); }
-          return table_or_zero(cards, w);
-        };
-        auto row_w = [&](int i) { return C.stride[i]; };
-        auto up_w = [&](int i) { return i < C.n_up ? C.stride[i] / C.R : (int64_t)0; };
-        auto sep_w = [&](int ch) {
-          return [&, ch](int i) -> int64_t {
-            const HostClique &K = P.cl[ch];
-            for (int q = 0; q < K.n_up; ++q)
-              if (K.vars[q] == C.vars[i]) return K.stride[q] / K.R;
-            return 0;
-          };
-        };
-        DMulti M{};
-        M.nF = nF;
-        M.nX = 1;
-        for (int i : Xv) M.nX *= C.card[i];
-        M.nU = 1;
-        for (int i : Uv) M.nU *= C.card[i];
-        M.Ef = tab(Fv, row_w); M.Ex = tab(Xv, row_w); M.Eu = tab(Uv, row_w);
-        M.Sf = tab(Fv, up_w); M.Sx = tab(Xv, up_w); M.Su = tab(Uv, up_w);
-        M.T1f = tab(Fv, sep_w(prim)); M.T1x = tab(Xv, sep_w(prim));
-        M.prim_row = sep_row[prim];
-        M.clique = c;
-        M.nsec = (int)secs.size();
-        int off = 0;
-        for (int j = 0; j < M.nsec; ++j) {
-          const int ch = secs[j];
-          const std::vector<int> Sj = sep_vars(ch);
-          // local space L = S_j \ F (inside U), in the clique's layout order
-          std::vector<int> Lpos;
-          for (int i : Uv)
-            if (std::find(Sj.begin(), Sj.end(), C.vars[i]) != Sj.end()) Lpos.push_back(i);
-          std::vector<int64_t> lstride(C.vars.size(), 0);
-          int64_t ls = 1;
-          for (int q = (int)Lpos.size() - 1; q >= 0; --q) { lstride[Lpos[q]] = ls; ls *= C.card[Lpos[q]]; }
-          DMultiSec &S = M.sec[j];
-          S.nl = (int32_t)ls;
-          S.acc_off = off;
-          off += (int)ls;
-          S.Au = tab(Uv, [&](int i) { return lstride[i]; });
-          S.Tf = tab(Fv, sep_w(ch));
-          S.Tl = tab(Lpos, sep_w(ch));
-          S.dst_row = sep_row[ch];
-        }
-        M.acc_rows = off;
-        P.max_acc_rows = std::max(P.max_acc_rows, off);
-        multi_of[c] = (int)P.dmulti.size();
-        P.dmulti.push_back(M);
-      }
-    }
-    for (int ch : kids) {
-      if (std::find(fused.begin(), fused.end(), ch) != fused.end()) continue;
+    for (int ch : C.children) {
       const HostClique &K = P.cl[ch];
+      if (K.n_up == 0) continue;
       std::vector<int> sv(K.vars.begin(), K.vars.begin() + K.n_up);
       make_task(sv, TASK_CHILD, ch, sep_row[ch]);
     }
@@ -771,22 +646,21 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   const int NW = 8;  // warps per block
   // Rows per warp item: fixed by the option (rows per block / warps), else
   // chosen per layer so that a layer has about items_per_tile (default 192)
-  // warp items per case tile,
-  // between 32 rows (one index batch) and 512: a small layer is
-  // latency-bound and finishes sooner in short items, a big one amortises
-  // each item's set-up over long ones.
+  // warp items per case tile, between a minimum (32 rows, one index batch,
+  // for collect; 16 for distribute, whose rows carry less work) and 512: a
+  // small layer is latency-bound and finishes sooner in short items, a big
+  // one amortises each item's set-up over long ones.
   P.rows_per_cta = opts.rows_per_cta > 0 ? opts.rows_per_cta : 0;
   auto layer_rows = [&](int64_t total, bool distribute) -> int64_t {
     if (opts.rows_per_cta > 0) return std::max<int64_t>(1, opts.rows_per_cta / NW);
     int64_t items = opts.items_per_tile > 0 ? opts.items_per_tile : 192;
     if (distribute && opts.items_per_tile_distribute > 0) items = opts.items_per_tile_distribute;
-    int64_t r = 32;
+    int64_t r = distribute ? 16 : 32;
     while (r < 512 && r * 2 * items <= total) r *= 2;
     return r;
   };
   P.citems.clear();
   P.ditems.clear();
-  P.mitems.clear();
   P.n_groups = 0;
   P.n_partials = 0;
   // one item per warp: whole segments when a segment fits the warp's rows,
@@ -845,7 +719,6 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       if (P.cl[c].depth != L) continue;
       crows += P.cl[c].size;
       for (int t : tasks_of[c]) drows += P.dtask[t].T * P.dtask[t].U;
-      if (multi_of[c] >= 0) drows += P.cl[c].size;
     }
     const int64_t cR = layer_rows(crows, false), dR = layer_rows(drows, true);
     for (int c = 0; c < m; ++c) {
@@ -860,27 +733,6 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       for (int t : tasks_of[c]) emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U, dR);
     }
     lv.d_item_end = (int64_t)P.ditems.size();
-    // fused multi-child tasks: items of whole F-blocks
-    lv.m_item_begin = (int64_t)P.mitems.size();
-    for (int c = 0; c < m; ++c) {
-      if (P.cl[c].depth != L || multi_of[c] < 0) continue;
-      const DMulti &M = P.dmulti[multi_of[c]];
-      lv.m_max_acc = std::max(lv.m_max_acc, M.acc_rows);
-      const int64_t block = M.nX * M.nU;
-      const int64_t per = std::max<int64_t>(1, dR / block);
-      for (int64_t f0 = 0; f0 < M.nF; f0 += per) {
-        DItem it{};
-        it.t0 = f0;
-        it.nt = std::min(per, M.nF - f0);
-        it.nu = block;
-        it.task = multi_of[c];
-        it.npieces = 1;
-        it.group = -1;
-        it.partial = -1;
-        P.mitems.push_back(it);
-      }
-    }
-    lv.m_item_end = (int64_t)P.mitems.size();
   }
   P.base_exp_sum = 0;
   for (int c = 0; c < m; ++c) P.base_exp_sum += base_exp[c];

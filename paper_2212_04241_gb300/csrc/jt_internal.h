@@ -70,39 +70,10 @@ struct DTask {
   int32_t src_sep;
 };
 
-// A fused distribute task of a clique with several children: the clique's
-// rows are visited block by block, a block fixing the digits of F = S1 ∩ S2
-// (S1 the largest child separator, the "primary").  Inside a block the
-// primary child's entries complete one after another (x over S1 \ F, u over
-// C \ S1); every secondary child shares exactly F with S1, so its remaining
-// variables lie in C \ S1 and its entries complete at the end of the block
-// from per-warp accumulators.  One pass over psi replaces one pass per child.
-constexpr int kMaxSec = 3;
-constexpr int kMaxAccRows = 8;
-struct DMultiSec {
-  int64_t Au;         // pool table over U: local index of the secondary entry
-  int64_t Tf, Tl;     // pool tables over F and over the local space: entry index
-  int64_t dst_row;    // the secondary child's sep_row
-  int32_t nl;         // local entries (product of cards of S_i \ F)
-  int32_t acc_off;    // first accumulator row
-};
-struct DMulti {
-  int64_t nF, nX, nU;
-  int64_t Ef, Ex, Eu;     // row offsets in the clique (pool tables over F, X, U)
-  int64_t Sf, Sx, Su;     // entries of the clique's upward separator (rho index)
-  int64_t T1f, T1x;       // primary child's separator entry
-  int64_t prim_row;       // primary child's sep_row
-  int32_t clique;
-  int32_t nsec;
-  int32_t acc_rows;
-  int32_t pad;
-  DMultiSec sec[kMaxSec];
-};
-
-// One thread block of a layer launch (the same list serves every tile).
-//   split == 0: the block owns segments [t0, t0+nt), one warp per segment
-//   split == 1: the block owns rows [u0, u0+nu) of segment t0; when the
-//               segment has several pieces, the block writes a partial sum
+// One warp's work item in a layer launch (the same list serves every tile).
+//   split == 0: the warp owns segments [t0, t0+nt)
+//   split == 1: the warp owns rows [u0, u0+nu) of segment t0; when the
+//               segment has several pieces, the warp writes a partial sum
 //               and the last piece to finish combines them in piece order
 struct DItem {
   int64_t t0, nt;
@@ -148,8 +119,6 @@ struct Level {
   // collect and distribute work of one tree layer
   int64_t c_item_begin = 0, c_item_end = 0;   // into collect_items
   int64_t d_item_begin = 0, d_item_end = 0;   // into distribute_items
-  int64_t m_item_begin = 0, m_item_end = 0;   // into multi_items (fused multi-child tasks)
-  int m_max_acc = 0;                           // most accumulator rows of a fused task in the layer
   int c_max_maps = 0;                          // most maps of a clique in the layer
 };
 
@@ -176,9 +145,7 @@ struct Plan {
   std::vector<DClique> dcl;
   std::vector<DMap> dmap;
   std::vector<DTask> dtask;
-  std::vector<DItem> citems, ditems, mitems;
-  std::vector<DMulti> dmulti;
-  int32_t max_acc_rows = 0;       // largest accumulator of a fused multi-child task
+  std::vector<DItem> citems, ditems;
   std::vector<Level> levels;      // index = depth
   std::vector<int32_t> ipool;     // int32 index tables
   std::vector<float> base32;

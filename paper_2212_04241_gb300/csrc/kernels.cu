@@ -34,9 +34,8 @@ namespace jt {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kGroup = 4;  // rows whose loads a warp issues together (fused tasks)
-// The same for the layer kernels, by cases per thread: a group holds
-// 16 cases per lane at most, so wider tiles load fewer rows at once.
+// Rows whose loads a warp issues together, by kernel and cases per thread:
+// a group holds 16 cases per lane at most, so wider tiles load fewer rows.
 template <int CPT>
 constexpr int kCollectGroup = CPT >= 8 ? 2 : 4;
 template <int CPT>
@@ -546,151 +545,6 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
 }
 
 // ---------------------------------------------------------------------------
-// distribute, fused multi-child tasks (see DMulti)
-// ---------------------------------------------------------------------------
-constexpr int kMultiWarps = 8;  // warps (independent items) per block
-
-template <int CPT>
-__global__ void __launch_bounds__(32 * kMultiWarps, kDistributeBlocksPerSM) k_distribute_multi(DevPlan P, DevArena A, int64_t item_begin,
-                                                                        int64_t n_items, int acc_rows_max) {
-  constexpr int W = 32 * CPT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t iw = (int64_t)blockIdx.x * kMultiWarps + warp;
-  if (iw >= n_items) return;
-  // this warp's secondary accumulators: rows of W cases; every add is a
-  // compensated run sum of consecutive rows
-  float *acc = reinterpret_cast<float *>(smem_raw) + (size_t)warp * acc_rows_max * W;
-  const DItem it = P.mitems[item_begin + iw];
-  const DMulti &M = P.multis[it.task];
-  const int tile = blockIdx.y;
-  const DClique C = P.cl[M.clique];
-  const float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
-  const float *rho = A.rho + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
-  const bool root = C.is_root != 0;
-  Vec<CPT> rs;
-#pragma unroll
-  for (int k = 0; k < CPT; ++k)
-    rs.x[k] = root ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + M.clique) * W + col_of<CPT>(lane, k)]))
-                   : 1.f;
-  const int nsec = M.nsec;
-  for (int a = 0; a < M.acc_rows; ++a) strow<CPT>(acc + (size_t)a * W, lane, vzero<CPT>());
-  const int32_t *__restrict__ Ef = P.ipool + M.Ef;
-  const int32_t *__restrict__ Ex = P.ipool + M.Ex;
-  const int32_t *__restrict__ Eu = P.ipool + M.Eu;
-  const int32_t *__restrict__ Sf = P.ipool + M.Sf;
-  const int32_t *__restrict__ Sx = P.ipool + M.Sx;
-  const int32_t *__restrict__ Su = P.ipool + M.Su;
-  const int32_t *__restrict__ T1f = P.ipool + M.T1f;
-  const int32_t *__restrict__ T1x = P.ipool + M.T1x;
-  const int32_t nX = (int32_t)M.nX, nU = (int32_t)M.nU, XU = nX * nU;
-
-  // rho_child[t] = value / phi*_child[t], 0/0 := 0
-  auto ratio_out = [&](int64_t row, const Vec<CPT> &val) {
-    const int64_t o = ((int64_t)tile * P.sep_rows + row) * W;
-    const Vec<CPT> ph = ldrow<CPT>(A.phistar + o, lane);
-    Vec<CPT> q;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) q.x[k] = (ph.x[k] > 0.f) ? val.x[k] / ph.x[k] : 0.f;
-    strow<CPT>(A.rho + o, lane, q);
-  };
-
-  const int32_t count = (int32_t)(it.nt * (int64_t)XU);
-  Vec<CPT> sum = vzero<CPT>(), comp = vzero<CPT>(), part = vzero<CPT>();
-  // per secondary: the accumulator row being summed in registers (Kahan)
-  Vec<CPT> sp[kMaxSec], spc[kMaxSec];
-  int32_t scur[kMaxSec];
-#pragma unroll
-  for (int i = 0; i < kMaxSec; ++i) { sp[i] = vzero<CPT>(); spc[i] = vzero<CPT>(); scur[i] = -1; }
-  auto sec_flush = [&](int i) {
-    if (scur[i] < 0) return;
-    float *a = acc + (size_t)(M.sec[i].acc_off + scur[i]) * W;
-    Vec<CPT> as = ldrow<CPT>(a, lane);
-    vadd<CPT>(as, sp[i]);
-    strow<CPT>(a, lane, as);
-    sp[i] = vzero<CPT>();
-    spc[i] = vzero<CPT>();
-  };
-  for (int32_t b0 = 0; b0 < count; b0 += 32) {
-    const int nb = min(32, count - b0);
-    // lane j: row b0 + j, flattened as (block f, x, u)
-    const int32_t q = b0 + min(lane, nb - 1);
-    const int32_t fb = q / XU, rem = q - fb * XU;
-    const int32_t f = (int32_t)it.t0 + fb, x = rem / nU, u = rem - (rem / nU) * nU;
-    const int32_t ej = __ldg(Ef + f) + __ldg(Ex + x) + __ldg(Eu + u);
-    const int32_t xj = root ? 0 : __ldg(Sf + f) + __ldg(Sx + x) + __ldg(Su + u);
-    const int32_t t1j = __ldg(T1f + f) + __ldg(T1x + x);
-    int32_t lj[kMaxSec];
-#pragma unroll
-    for (int i = 0; i < kMaxSec; ++i) lj[i] = i < nsec ? __ldg(P.ipool + M.sec[i].Au + u) : 0;
-    const unsigned lastU = __ballot_sync(kFull, u == nU - 1 && lane < nb);
-    const unsigned lastB = __ballot_sync(kFull, u == nU - 1 && x == nX - 1 && lane < nb);
-    for (int r = 0; r < nb; r += kGroup) {
-      Vec<CPT> p[kGroup];
-#pragma unroll
-      for (int g = 0; g < kGroup; ++g)
-        p[g] = ldrow<CPT, LD_STREAM>(psi + (int64_t)__shfl_sync(kFull, ej, min(r + g, nb - 1)) * W, lane);
-      if (!root) {
-        Vec<CPT> qv[kGroup];
-#pragma unroll
-        for (int g = 0; g < kGroup; ++g)
-          qv[g] = ldrow<CPT, LD_NC>(rho + (int64_t)__shfl_sync(kFull, xj, min(r + g, nb - 1)) * W, lane);
-#pragma unroll
-        for (int g = 0; g < kGroup; ++g) vmul<CPT>(p[g], qv[g]);
-      } else {
-#pragma unroll
-        for (int g = 0; g < kGroup; ++g) vmul<CPT>(p[g], rs);
-      }
-#pragma unroll
-      for (int g = 0; g < kGroup; ++g) {
-        if (r + g < nb) {
-          vadd<CPT>(part, p[g]);
-#pragma unroll
-          for (int i = 0; i < kMaxSec; ++i) {
-            if (i < nsec) {
-              const int32_t l = __shfl_sync(kFull, lj[i], r + g);
-              if (l != scur[i]) {  // a new accumulator row: bank the old one
-                sec_flush(i);
-                scur[i] = l;
-              }
-              Vec<CPT> v = p[g];
-              kahan_fold<CPT>(sp[i], spc[i], v);
-            }
-          }
-          if ((lastU >> (r + g)) & 1u) {  // a primary entry is complete
-            kahan_fold<CPT>(sum, comp, part);
-            ratio_out(M.prim_row + __shfl_sync(kFull, t1j, r + g), sum);
-            sum = vzero<CPT>();
-            comp = vzero<CPT>();
-          }
-          if ((lastB >> (r + g)) & 1u) {  // the block is complete: secondary entries
-            const int32_t fdone = __shfl_sync(kFull, f, r + g);
-#pragma unroll
-            for (int i = 0; i < kMaxSec; ++i) {
-              if (i < nsec) {
-                sec_flush(i);
-                scur[i] = -1;
-              }
-            }
-            for (int i = 0; i < nsec; ++i) {
-              const DMultiSec &S = M.sec[i];
-              const int32_t tbase = __ldg(P.ipool + S.Tf + fdone);
-              for (int l = 0; l < S.nl; ++l) {
-                float *a = acc + (size_t)(S.acc_off + l) * W;
-                const Vec<CPT> val = ldrow<CPT>(a, lane);
-                strow<CPT>(a, lane, vzero<CPT>());
-                ratio_out(S.dst_row + tbase + __ldg(P.ipool + S.Tl + l), val);
-              }
-            }
-          }
-        }
-      }
-      kahan_fold<CPT>(sum, comp, part);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // finalize, part 1: log P(e) and status, one thread per case
 // ---------------------------------------------------------------------------
 constexpr int kStageCols = 16;
@@ -911,22 +765,6 @@ void launch_collect(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int
   else collect_t<1>(P, A, b, n, max_maps, s);
 }
 
-template <int CPT>
-static void multi_t(const DevPlan &P, const DevArena &A, int64_t b, int64_t n, int acc_rows, cudaStream_t s) {
-  dim3 grid((unsigned)((n + kMultiWarps - 1) / kMultiWarps), (unsigned)A.tiles);
-  const size_t smem = sizeof(float) * (size_t)kMultiWarps * acc_rows * 32 * CPT;
-  k_distribute_multi<CPT><<<grid, 32 * kMultiWarps, smem, s>>>(P, A, b, n, acc_rows);
-}
-
-void launch_distribute_multi(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, int acc_rows,
-                             cudaStream_t s) {
-  if (n <= 0) return;
-  if (cpt == 8) multi_t<8>(P, A, b, n, acc_rows, s);
-  else if (cpt == 4) multi_t<4>(P, A, b, n, acc_rows, s);
-  else if (cpt == 2) multi_t<2>(P, A, b, n, acc_rows, s);
-  else multi_t<1>(P, A, b, n, acc_rows, s);
-}
-
 void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   dim3 grid((unsigned)((n + kWarps - 1) / kWarps), (unsigned)A.tiles);
@@ -934,16 +772,6 @@ void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, 
   else if (cpt == 4) k_distribute<4><<<grid, kThreads, 0, s>>>(P, A, b, n);
   else if (cpt == 2) k_distribute<2><<<grid, kThreads, 0, s>>>(P, A, b, n);
   else k_distribute<1><<<grid, kThreads, 0, s>>>(P, A, b, n);
-}
-
-cudaError_t configure_distribute_smem(int cpt, int acc_rows) {
-  const size_t bytes = sizeof(float) * (size_t)kMultiWarps * acc_rows * 32 * cpt;
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  auto set = [&](const void *f) { return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); };
-  if (cpt == 8) return set((const void *)k_distribute_multi<8>);
-  if (cpt == 4) return set((const void *)k_distribute_multi<4>);
-  if (cpt == 2) return set((const void *)k_distribute_multi<2>);
-  return set((const void *)k_distribute_multi<1>);
 }
 
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,

@@ -16,8 +16,6 @@ struct DevPlan {
   const DTask *tasks;
   const DItem *citems;
   const DItem *ditems;
-  const DItem *mitems;
-  const DMulti *multis;
   const int32_t *ipool;
   const float *base32;
   const int32_t *card;       // [n]
@@ -69,11 +67,8 @@ void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cas
 size_t collect_smem_bytes(int cpt, int max_maps);        // block (capped at kCollectSmemLimit)
 size_t collect_warp_smem_bytes(int cpt, int max_maps);   // one warp
 constexpr size_t kCollectSmemLimit = 220 * 1024;
-// raise the dynamic shared-memory limits of the layer kernels (once per plan)
+// raise the dynamic shared-memory limit of the collect kernel (once per plan)
 cudaError_t configure_collect_smem(int cpt, size_t bytes);
-cudaError_t configure_distribute_smem(int cpt, int acc_rows);
-void launch_distribute_multi(int cpt, const DevPlan &P, const DevArena &A, int64_t item_begin, int64_t n_items,
-                             int acc_rows, cudaStream_t s);
 constexpr int kMaxTilesPerChunk = 16384;
 
 // plain FP64 path

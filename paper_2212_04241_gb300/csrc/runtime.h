@@ -70,7 +70,7 @@ jt_status run_chunk(jt_plan *pl, Arena &a, const int32_t *d_ev, int32_t nc, doub
 // bounded wait on this arena; call after synchronising its stream
 jt_status check_arena_flag(Arena &a);
 int budget_tiles(const jt_plan *pl, int64_t budget_bytes);
-// the launches of one tree layer (collect, or distribute incl. fused tasks)
+// the launch of one tree layer (collect or distribute)
 void enqueue_collect_layer(const jt_plan *pl, const DevArena &A, int layer, cudaStream_t s);
 void enqueue_distribute_layer(const jt_plan *pl, const DevArena &A, int layer, cudaStream_t s);
 }  // namespace jt

@@ -31,8 +31,7 @@ class CompileOpts(ctypes.Structure):
                 ("cases_per_thread", ctypes.c_int32), ("rows_per_cta", ctypes.c_int32),
                 ("max_clique_entries", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
                 ("use_graphs", ctypes.c_int32), ("items_per_tile", ctypes.c_int32),
-                ("items_per_tile_distribute", ctypes.c_int32), ("fuse_children", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("items_per_tile_distribute", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -44,8 +43,7 @@ class PlanInfo(ctypes.Structure):
                 ("arena_bytes", ctypes.c_int64), ("static_device_bytes", ctypes.c_int64),
                 ("collect_items", ctypes.c_int64), ("distribute_items", ctypes.c_int64),
                 ("algorithmic_bytes_per_case", ctypes.c_double),
-                ("kernels_per_chunk", ctypes.c_int32), ("fused_tasks", ctypes.c_int32),
-                ("separator_evidence_vars", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("kernels_per_chunk", ctypes.c_int32), ("separator_evidence_vars", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

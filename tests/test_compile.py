@@ -120,12 +120,6 @@ def test_algorithmic_bytes_formula():
     assert info["algorithmic_bytes_per_case"] == expect
 
 
-def test_fused_tasks_counted():
-    net = configs.network("bn60")
-    assert J.Plan(net, host_only=1, fuse_children=1).info()["fused_tasks"] > 0
-    assert J.Plan(net, host_only=1).info()["fused_tasks"] == 0
-
-
 @pytest.mark.parametrize("name", ["bn20", "bn60", "bn110", "bn420", "bn1000"])
 def test_evidence_placement_smallest_table(name):
     """Each variable's evidence indicator enters the smallest table holding

@@ -15,7 +15,7 @@ import pytest
 import oracle
 from synth import configs, empty_evidence
 from synth.bn import tiny_random_network, sample_cases
-from tests.common import assert_parity32, golden_cases, max_logpe_err
+from tests.common import assert_parity32, golden_cases
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +61,7 @@ def test_bn60_full_batch_all_cases():
 
 
 @pytest.mark.parametrize("opts", [dict(cases_per_thread=1), dict(cases_per_thread=2), dict(cases_per_thread=4),
-                                  dict(use_graphs=0), dict(root_rule=J.JT_ROOT_LARGEST), dict(fuse_children=1),
+                                  dict(use_graphs=0), dict(root_rule=J.JT_ROOT_LARGEST),
                                   dict(rows_per_cta=64), dict(rows_per_cta=4096)])
 def test_bn60_option_variants(opts):
     net = configs.network("bn60")
@@ -239,23 +239,3 @@ def test_autotuned_plan_parity():
     assert ns > 0
     p = J.Plan(net, **opts)
     assert_parity32(*p.infer(ev), *_oracle(net, ev), where=f"autotuned {opts}")
-
-
-@pytest.mark.parametrize("name", ["bn60", "bn110", "bn420"])
-def test_fused_child_messages_match_separate_passes(name):
-    """One pass for several child messages gives the same results as one
-    pass per child (both within the FP32 tolerance of the oracle)."""
-    net = configs.network(name)
-    n = {"bn60": 600, "bn110": 96, "bn420": 64}[name]
-    ev = configs.evidence(name, net, n_cases=n)
-    fused = J.Plan(net, fuse_children=1)
-    assert fused.info()["fused_tasks"] > 0
-    sep = J.Plan(net)
-    assert sep.info()["fused_tasks"] == 0
-    a = fused.infer(ev)
-    b = sep.infer(ev)
-    assert np.array_equal(a[2], b[2])
-    assert np.max(np.abs(a[1] - b[1])) <= 2e-6
-    assert max_logpe_err(a[0], b[0]) <= 1e-7
-    idx = np.arange(0, n, max(1, n // 24))
-    assert_parity32(a[0][idx], a[1][idx], a[2][idx], *_oracle(net, ev[idx]), where=f"{name} fused")
