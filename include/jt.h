@@ -79,6 +79,14 @@ enum {
                             ties: larger table, then lowest id */
 };
 
+/* Work order of a pass.  LAYERS: one launch per tree layer, every clique
+ * of the layer for every case tile, each launch waiting for the previous
+ * one (Section 2's layer-by-layer order).  DATAFLOW: one launch per pass;
+ * case tiles are independent, so a clique's work on a tile starts as soon
+ * as its own producers on that tile are done, and the small layers near the
+ * root of one tile overlap the large layers of others. */
+enum { JT_SCHEDULE_DATAFLOW = 0, JT_SCHEDULE_LAYERS = 1 };
+
 typedef struct {
   int32_t root_rule;          /* JT_ROOT_* (default JT_ROOT_MIN_HEIGHT) */
   int32_t host_only;          /* 1: compile on the host only, allocate no
@@ -102,7 +110,9 @@ typedef struct {
                                  0 = automatic (192) */
   int32_t items_per_tile_distribute; /* the same for the distribute pass;
                                  0 = items_per_tile */
-  int32_t reserved[5];
+  int32_t schedule;           /* JT_SCHEDULE_*: how the work of a pass is
+                                 ordered on the GPU (default dataflow) */
+  int32_t reserved[4];
 } jt_compile_opts;
 
 typedef struct {

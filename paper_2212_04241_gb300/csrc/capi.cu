@@ -41,7 +41,8 @@ ArenaLayout arena_layout(const Plan &P) {
   L.counters = align_up(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, P.n_groups));
   L.ev = align_up(sizeof(int32_t) * W * (size_t)P.n);
   L.bad = align_up(sizeof(int32_t) * W);
-  L.per_tile = L.psi + 2 * L.sep + L.post + L.partial + L.maxbits + L.counters + L.ev + L.bad;
+  L.ready = align_up(sizeof(uint32_t) * 2 * P.cl.size());
+  L.per_tile = L.psi + 2 * L.sep + L.post + L.partial + L.maxbits + L.counters + L.ev + L.bad + L.ready;
   return L;
 }
 
@@ -71,7 +72,9 @@ static void arena_bind(const Plan &P, Arena &a, char *mem, int tiles) {
   a.da.counters = reinterpret_cast<uint32_t *>(take(L.counters));
   a.da.ev = reinterpret_cast<int32_t *>(take(L.ev));
   a.da.bad = reinterpret_cast<int32_t *>(take(L.bad));
+  a.da.ready = reinterpret_cast<uint32_t *>(take(L.ready));
   a.da.errflag = reinterpret_cast<uint32_t *>(mem + off);
+  a.da.queue = reinterpret_cast<unsigned long long *>(mem + off + ArenaLayout::kQueueOffset);
   off += ArenaLayout::kTail;
   a.da.tiles = tiles;
   a.mem = mem;
@@ -123,12 +126,25 @@ void enqueue_distribute_layer(const jt_plan *pl, const DevArena &A, int L, cudaS
 
 // Enqueue the layer launches of one chunk: collect deepest layer first,
 // then distribute from the root down (Section 2's BFS layers).
-static void enqueue_layers(const jt_plan *pl, const DevArena &A, cudaStream_t s) {
+void enqueue_passes(const jt_plan *pl, const DevArena &A, cudaStream_t s) {
   const Plan &P = pl->P;
-  cudaMemsetAsync(A.maxbits, 0, arena_layout(P).maxbits * (size_t)A.tiles, s);
-  for (int L = P.height; L >= 0; --L) enqueue_collect_layer(pl, A, L, s);
-  for (int L = 0; L <= P.height; ++L) enqueue_distribute_layer(pl, A, L, s);
+  const ArenaLayout L = arena_layout(P);
+  cudaMemsetAsync(A.maxbits, 0, L.maxbits * (size_t)A.tiles, s);
+  if (P.opts.schedule == JT_SCHEDULE_LAYERS) {
+    for (int l = P.height; l >= 0; --l) enqueue_collect_layer(pl, A, l, s);
+    for (int l = 0; l <= P.height; ++l) enqueue_distribute_layer(pl, A, l, s);
+    return;
+  }
+  // dataflow: fresh per-tile counters and unit counters for this chunk
+  cudaMemsetAsync(A.ready, 0, L.ready * (size_t)A.tiles, s);
+  cudaMemsetAsync(A.queue, 0, ArenaLayout::kTail - ArenaLayout::kQueueOffset, s);
+  int max_maps = 0;
+  for (const Level &lv : P.levels) max_maps = std::max(max_maps, lv.c_max_maps);
+  launch_collect_flow(P.cpt_per_thread, pl->dp, A, pl->flow_collect_blocks, max_maps, s);
+  launch_distribute_flow(P.cpt_per_thread, pl->dp, A, pl->flow_distribute_blocks, s);
 }
+
+static void enqueue_layers(const jt_plan *pl, const DevArena &A, cudaStream_t s) { enqueue_passes(pl, A, s); }
 
 static jt_status graph_for(jt_plan *pl, Arena &a, int tiles, cudaGraphExec_t *out) {
   auto it = a.graphs.find(tiles);
@@ -250,6 +266,9 @@ static jt_status upload_plan(jt_plan *pl) {
   const size_t o_b32 = put(blob, P.base32), o_card = put(blob, card32), o_po = put(blob, P.post_off);
   const size_t o_cp = put(blob, P.comp_ptr), o_cv = put(blob, P.comp_vars), o_cc = put(blob, P.comp_cliques);
   const size_t o_cr = put(blob, P.comp_roots), o_pg = put(blob, P.pgroup_ptr);
+  const size_t o_cfp = put(blob, P.c_flow_pref), o_cfb = put(blob, P.c_flow_begin);
+  const size_t o_dfp = put(blob, P.d_flow_pref), o_dfb = put(blob, P.d_flow_begin);
+  const size_t o_cn = put(blob, P.c_need), o_cno = put(blob, P.c_notify), o_dn = put(blob, P.d_need);
   JT_CUDA_TRY(cudaMalloc(&pl->d_static, blob.size()));
   pl->static_bytes = blob.size();
   JT_CUDA_TRY(cudaMemcpy(pl->d_static, blob.data(), blob.size(), cudaMemcpyHostToDevice));
@@ -270,6 +289,14 @@ static jt_status upload_plan(jt_plan *pl) {
   D.comp_roots = reinterpret_cast<const int32_t *>(b + o_cr);
   D.n_comp = (int32_t)P.comp_roots.size();
   D.pgroup_ptr = reinterpret_cast<const int32_t *>(b + o_pg);
+  D.c_flow_pref = reinterpret_cast<const int64_t *>(b + o_cfp);
+  D.c_flow_begin = reinterpret_cast<const int64_t *>(b + o_cfb);
+  D.d_flow_pref = reinterpret_cast<const int64_t *>(b + o_dfp);
+  D.d_flow_begin = reinterpret_cast<const int64_t *>(b + o_dfb);
+  D.c_need = reinterpret_cast<const uint32_t *>(b + o_cn);
+  D.c_notify = reinterpret_cast<const int32_t *>(b + o_cno);
+  D.d_need = reinterpret_cast<const uint32_t *>(b + o_dn);
+  D.n_flow_layers = P.height + 1;
   D.n_pgroups = (int32_t)P.pgroup_ptr.size() - 1;
   D.n_vars = P.n;
   D.n_cliques = (int32_t)P.cl.size();
@@ -287,6 +314,10 @@ static jt_status upload_plan(jt_plan *pl) {
     return JT_ETOOBIG;
   }
   JT_CUDA_TRY(configure_collect_smem(P.cpt_per_thread, smem));
+  int sms = 0;
+  JT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
+  pl->flow_collect_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, true, max_maps);
+  pl->flow_distribute_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, false, 0);
   return JT_OK;
 }
 
@@ -378,9 +409,13 @@ extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
   o->algorithmic_bytes_per_case = 8.0 * (double)P.sum_cl + 16.0 * (double)P.sum_sep + 4.0 * P.n +
                                   8.0 * (double)P.sum_card + 8.0;
   int k = 3;  // evidence + log P(e) + posteriors
-  for (const Level &lv : P.levels) {
-    k += lv.c_item_end > lv.c_item_begin;
-    k += lv.d_item_end > lv.d_item_begin;
+  if (P.opts.schedule == JT_SCHEDULE_LAYERS) {
+    for (const Level &lv : P.levels) {
+      k += lv.c_item_end > lv.c_item_begin;
+      k += lv.d_item_end > lv.d_item_begin;
+    }
+  } else {
+    k += 2;  // one dataflow launch per pass
   }
   o->kernels_per_chunk = k;
   o->separator_evidence_vars = 0;
@@ -668,6 +703,20 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
     int e0 = mark();
     launch_evidence(P.cpt_per_thread, d_ev + b * P.n, nc, pl->dp, A, s);
     spans.push_back({e0, mark(), 2});
+    if (P.opts.schedule != JT_SCHEDULE_LAYERS) {
+      // dataflow: one span per pass (the counters are reset inside the first)
+      int max_maps = 0;
+      for (const Level &lv : P.levels) max_maps = std::max(max_maps, lv.c_max_maps);
+      JT_CUDA_TRY(cudaMemsetAsync(A.maxbits, 0, arena_layout(P).maxbits * (size_t)A.tiles, s));
+      JT_CUDA_TRY(cudaMemsetAsync(A.ready, 0, arena_layout(P).ready * (size_t)A.tiles, s));
+      JT_CUDA_TRY(cudaMemsetAsync(A.queue, 0, ArenaLayout::kTail - ArenaLayout::kQueueOffset, s));
+      int a = mark();
+      launch_collect_flow(P.cpt_per_thread, pl->dp, A, pl->flow_collect_blocks, max_maps, s);
+      spans.push_back({a, mark(), 0});
+      a = mark();
+      launch_distribute_flow(P.cpt_per_thread, pl->dp, A, pl->flow_distribute_blocks, s);
+      spans.push_back({a, mark(), 1});
+    } else {
     JT_CUDA_TRY(cudaMemsetAsync(A.maxbits, 0, arena_layout(P).maxbits * (size_t)A.tiles, s));
     for (int L = P.height; L >= 0; --L) {
       const Level &lv = P.levels[L];
@@ -683,6 +732,7 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
       int a = mark();
       enqueue_distribute_layer(pl, A, L, s);
       spans.push_back({a, mark(), 1});
+    }
     }
     int f0 = mark();
     launch_finalize(P.cpt_per_thread, pl->dp, A, nc, P.dcl[P.root].sep_row, d_lp + b,

@@ -585,6 +585,10 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     err = "cases_per_thread must be 1, 2, 4 or 8";
     return JT_EINVAL;
   }
+  if (opts.schedule != JT_SCHEDULE_DATAFLOW && opts.schedule != JT_SCHEDULE_LAYERS) {
+    err = "schedule must be JT_SCHEDULE_DATAFLOW or JT_SCHEDULE_LAYERS";
+    return JT_EINVAL;
+  }
   P.tile = 32 * P.cpt_per_thread;
   // distribute tasks: children first (ascending), then owned posteriors
   std::vector<std::vector<int>> tasks_of(m);
@@ -734,6 +738,35 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     }
     lv.d_item_end = (int64_t)P.ditems.size();
   }
+  // dataflow schedule: flow layers (collect deepest first, distribute from
+  // the root) and each clique's producers on its tile
+  P.c_flow_pref.assign(1, 0);
+  P.d_flow_pref.assign(1, 0);
+  P.c_flow_begin.clear();
+  P.d_flow_begin.clear();
+  for (int k = 0; k <= P.height; ++k) {
+    const Level &lc = P.levels[P.height - k];
+    P.c_flow_begin.push_back(lc.c_item_begin);
+    P.c_flow_pref.push_back(P.c_flow_pref.back() + (lc.c_item_end - lc.c_item_begin));
+    const Level &ld = P.levels[k];
+    P.d_flow_begin.push_back(ld.d_item_begin);
+    P.d_flow_pref.push_back(P.d_flow_pref.back() + (ld.d_item_end - ld.d_item_begin));
+  }
+  P.c_need.assign(m, 0);
+  P.d_need.assign(m, 0);
+  P.c_notify.assign(m, -1);
+  for (const DItem &it : P.citems) {
+    const HostClique &K = P.cl[it.task];
+    if (K.parent >= 0 && K.n_up > 0) {
+      P.c_notify[it.task] = K.parent;
+      ++P.c_need[K.parent];
+    }
+  }
+  for (const DItem &it : P.ditems) {
+    const DTask &T = P.dtask[it.task];
+    if (T.kind == TASK_CHILD) ++P.d_need[T.dst];
+  }
+
   P.base_exp_sum = 0;
   for (int c = 0; c < m; ++c) P.base_exp_sum += base_exp[c];
 

@@ -299,20 +299,18 @@ __host__ __device__ inline size_t collect_warp_smem(int cpt, int nm) {
          round16(sizeof(int32_t) * 32 * (size_t)nm);
 }
 
-template <int CPT>
-__global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPlan P, DevArena A, int64_t item_begin,
-                                                          int64_t n_items, int max_maps) {
+// One collect work item (a warp's rows of one clique, one case tile).  MSG
+// is the load path of the children's messages: the read-only path when an
+// earlier kernel wrote them, coherent loads when warps of the same kernel
+// did (dataflow schedule).
+template <int CPT, LoadMode MSG>
+__device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
+                                             unsigned char *ws, int max_maps, int lane) {
   constexpr int W = 32 * CPT;
   constexpr int G = kCollectGroup<CPT>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (iw >= n_items) return;
-  const DItem it = P.citems[item_begin + iw];
-  const int tile = blockIdx.y;
   const DClique C = P.cl[it.task];
   const int nm = C.map_end - C.map_begin;
-  unsigned char *ws = smem_raw + (size_t)warp * collect_warp_smem(CPT, max_maps);  // 16-byte aligned
+  // ws: this warp's shared memory (16-byte aligned), collect_warp_smem bytes
   float *mval = reinterpret_cast<float *>(ws);
   int64_t *mA = reinterpret_cast<int64_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps));
   int64_t *mB = mA + max_maps;
@@ -383,11 +381,11 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
         const float *mp1 = A.psi + mrow[two ? i + 1 : i];
         Vec<CPT> m0[G], m1[G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) m0[g] = ldrow<CPT, LD_NC>(mp0 + (int64_t)idx[i * 32 + min(r + g, nb - 1)] * W, lane);
+        for (int g = 0; g < G; ++g) m0[g] = ldrow<CPT, MSG>(mp0 + (int64_t)idx[i * 32 + min(r + g, nb - 1)] * W, lane);
         if (two) {
 #pragma unroll
           for (int g = 0; g < G; ++g)
-            m1[g] = ldrow<CPT, LD_NC>(mp1 + (int64_t)idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
+            m1[g] = ldrow<CPT, MSG>(mp1 + (int64_t)idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
         }
         {
           const Vec<CPT> sc = ldrow<CPT>(mval + i * W, lane);
@@ -452,19 +450,27 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
     if (mx.x[k] > 0.f) atomicMax(mb + col_of<CPT>(lane, k), __float_as_uint(mx.x[k]));
 }
 
-// ---------------------------------------------------------------------------
-// distribute
-// ---------------------------------------------------------------------------
 template <int CPT>
-__global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute(DevPlan P, DevArena A, int64_t item_begin,
-                                                             int64_t n_items) {
-  constexpr int W = 32 * CPT;
-  constexpr int G = kDistGroup<CPT>;
+__global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPlan P, DevArena A, int64_t item_begin,
+                                                          int64_t n_items, int max_maps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (iw >= n_items) return;
-  const DItem it = P.ditems[item_begin + iw];
-  const int tile = blockIdx.y;
+  collect_item<CPT, LD_NC>(P, A, P.citems[item_begin + iw], blockIdx.y,
+                           smem_raw + (size_t)warp * collect_warp_smem(CPT, max_maps), max_maps, lane);
+}
+
+// ---------------------------------------------------------------------------
+// distribute
+// ---------------------------------------------------------------------------
+// One distribute work item (a warp's rows of one task, one case tile).  RHO
+// is the load path of the clique's ratio rows (see collect_item).
+template <int CPT, LoadMode RHO>
+__device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
+                                                int lane) {
+  constexpr int W = 32 * CPT;
+  constexpr int G = kDistGroup<CPT>;
   const DTask T = P.tasks[it.task];
   const DClique C = P.cl[T.clique];
   // X rows: the clique's psi, or the phi* rows of its upward separator
@@ -516,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
         Vec<CPT> q[G];
 #pragma unroll
         for (int g = 0; g < G; ++g)
-          q[g] = ldrow<CPT, LD_NC>(rho + (int64_t)__shfl_sync(kFull, xj, min(r + g, nb - 1)) * W, lane);
+          q[g] = ldrow<CPT, RHO>(rho + (int64_t)__shfl_sync(kFull, xj, min(r + g, nb - 1)) * W, lane);
 #pragma unroll
         for (int g = 0; g < G; ++g) vmul<CPT>(p[g], q[g]);
       } else {
@@ -541,6 +547,134 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
   if (it.split) {
     Vec<CPT> tot;
     if (combine_split<CPT>(it, P, A, tile, lane, acc, tot)) output(it.t0, tot);
+  }
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute(DevPlan P, DevArena A, int64_t item_begin,
+                                                             int64_t n_items) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (iw >= n_items) return;
+  distribute_item<CPT, LD_NC>(P, A, P.ditems[item_begin + iw], blockIdx.y, lane);
+}
+
+// ---------------------------------------------------------------------------
+// dataflow schedule: one persistent launch per pass
+// ---------------------------------------------------------------------------
+//
+// Case tiles are independent, so a clique's collect work on tile k needs
+// only its children's collect work on tile k, and a clique's distribute
+// work on tile k only its parent's task for it on tile k.  A pass is one
+// launch: warps take units (work item, tile) from a global counter in tree
+// order (collect: deepest layer first; distribute: root first; tile-major
+// inside a layer), wait until the unit's producers on its tile have
+// finished (per-(tile, clique) counters), do the item, and count it done.
+// A unit only waits for units taken before it, and every taken unit is held
+// by a running warp, so the pass always completes.  Waits are bounded: a
+// wait that runs out sets the arena's error flag, every other wait then
+// gives up at once, and the host reports JT_ETIMEOUT.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Lane 0 waits until *ctr >= need and fences (acquire: the producers'
+// writes made before their counter increments are visible to it); the warp
+// barrier then orders those writes before every lane's later loads.
+__device__ __forceinline__ bool wait_ready(const uint32_t *ctr, uint32_t need, uint32_t *errflag, int lane) {
+  int ok = 1;
+  if (lane == 0) {
+    const volatile uint32_t *vc = ctr;
+    const volatile uint32_t *ve = errflag;
+    if (*vc < need) {
+      const unsigned long long t0 = global_ns();
+      unsigned ns = 32;
+      while (*vc < need) {
+        if (*ve != 0u) { ok = 0; break; }
+        if (global_ns() - t0 > kWaitLimitNs) {
+          atomicOr(errflag, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns *= 2;
+      }
+    }
+    __threadfence();
+  }
+  __syncwarp();
+  ok = __shfl_sync(kFull, ok, 0);
+  return ok != 0;
+}
+
+// A unit is done: every lane's writes are fenced, the warp synchronises, and
+// lane 0 publishes with a release (fence, then the counter increment).
+__device__ __forceinline__ void signal_done(uint32_t *ctr, int lane) {
+  __threadfence();
+  __syncwarp();
+  if (lane == 0 && ctr != nullptr) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+  }
+}
+
+// Next unit of a pass: returns false when the pass is exhausted; else the
+// item index and tile.  pref[k] = items of flow layers before k, begin[k]
+// = the first item of flow layer k in the pass's item list.
+__device__ __forceinline__ bool next_unit(unsigned long long *queue, const int64_t *pref, const int64_t *begin,
+                                          int n_layers, int tiles, int lane, int64_t &item, int &tile) {
+  long long u = 0;
+  if (lane == 0) u = (long long)atomicAdd(queue, 1ull);
+  u = __shfl_sync(kFull, u, 0);
+  if (u >= pref[n_layers] * (long long)tiles) return false;
+  const long long q = u / tiles;
+  int lo = 0, hi = n_layers - 1;  // largest k with pref[k] <= q
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  const long long local = u - pref[lo] * (long long)tiles;
+  const long long nk = pref[lo + 1] - pref[lo];
+  tile = (int)(local / nk);
+  item = begin[lo] + (local - (long long)tile * nk);
+  return true;
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect_flow(DevPlan P, DevArena A, int max_maps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char *ws = smem_raw + (size_t)warp * collect_warp_smem(CPT, max_maps);
+  int64_t item;
+  int tile;
+  while (next_unit(A.queue, P.c_flow_pref, P.c_flow_begin, P.n_flow_layers, A.tiles, lane, item, tile)) {
+    const DItem it = P.citems[item];
+    uint32_t *ready = A.ready + (int64_t)tile * 2 * P.n_cliques;
+    const uint32_t need = P.c_need[it.task];
+    if (need == 0u || wait_ready(ready + it.task, need, A.errflag, lane))
+      collect_item<CPT, LD_PLAIN>(P, A, it, tile, ws, max_maps, lane);
+    const int parent = P.c_notify[it.task];
+    signal_done(parent >= 0 ? ready + parent : nullptr, lane);
+  }
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute_flow(DevPlan P, DevArena A) {
+  const int lane = threadIdx.x & 31;
+  int64_t item;
+  int tile;
+  while (next_unit(A.queue + 16, P.d_flow_pref, P.d_flow_begin, P.n_flow_layers, A.tiles, lane, item, tile)) {
+    const DItem it = P.ditems[item];
+    const DTask &T = P.tasks[it.task];
+    uint32_t *ready = A.ready + ((int64_t)tile * 2 + 1) * P.n_cliques;
+    const uint32_t need = P.d_need[T.clique];
+    if (need == 0u || wait_ready(ready + T.clique, need, A.errflag, lane))
+      distribute_item<CPT, LD_PLAIN>(P, A, it, tile, lane);
+    signal_done(T.kind == TASK_CHILD ? ready + T.dst : nullptr, lane);
   }
 }
 
@@ -750,10 +884,16 @@ static void collect_t(const DevPlan &P, const DevArena &A, int64_t b, int64_t n,
 
 cudaError_t configure_collect_smem(int cpt, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  if (cpt == 8) return cudaFuncSetAttribute(k_collect<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (cpt == 4) return cudaFuncSetAttribute(k_collect<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (cpt == 2) return cudaFuncSetAttribute(k_collect<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return cudaFuncSetAttribute(k_collect<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  auto set = [&](const void *f) { return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); };
+  cudaError_t e = cpt == 8   ? set((const void *)k_collect<8>)
+                  : cpt == 4 ? set((const void *)k_collect<4>)
+                  : cpt == 2 ? set((const void *)k_collect<2>)
+                             : set((const void *)k_collect<1>);
+  if (e != cudaSuccess) return e;
+  if (cpt == 8) return set((const void *)k_collect_flow<8>);
+  if (cpt == 4) return set((const void *)k_collect_flow<4>);
+  if (cpt == 2) return set((const void *)k_collect_flow<2>);
+  return set((const void *)k_collect_flow<1>);
 }
 
 void launch_collect(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, int max_maps,
@@ -772,6 +912,53 @@ void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, 
   else if (cpt == 4) k_distribute<4><<<grid, kThreads, 0, s>>>(P, A, b, n);
   else if (cpt == 2) k_distribute<2><<<grid, kThreads, 0, s>>>(P, A, b, n);
   else k_distribute<1><<<grid, kThreads, 0, s>>>(P, A, b, n);
+}
+
+template <int CPT>
+static void collect_flow_t(const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s) {
+  const int nw = collect_warps(CPT, max_maps);
+  const size_t smem = (size_t)nw * collect_warp_smem(CPT, max_maps);
+  k_collect_flow<CPT><<<blocks, 32 * nw, smem, s>>>(P, A, max_maps);
+}
+
+void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s) {
+  if (cpt == 8) collect_flow_t<8>(P, A, blocks, max_maps, s);
+  else if (cpt == 4) collect_flow_t<4>(P, A, blocks, max_maps, s);
+  else if (cpt == 2) collect_flow_t<2>(P, A, blocks, max_maps, s);
+  else collect_flow_t<1>(P, A, blocks, max_maps, s);
+}
+
+void launch_distribute_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, cudaStream_t s) {
+  if (cpt == 8) k_distribute_flow<8><<<blocks, kThreads, 0, s>>>(P, A);
+  else if (cpt == 4) k_distribute_flow<4><<<blocks, kThreads, 0, s>>>(P, A);
+  else if (cpt == 2) k_distribute_flow<2><<<blocks, kThreads, 0, s>>>(P, A);
+  else k_distribute_flow<1><<<blocks, kThreads, 0, s>>>(P, A);
+}
+
+// Resident blocks per SM of the dataflow kernels (their grids fill the GPU once).
+template <class K>
+static int occupancy_of(K kernel, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+int flow_blocks_per_sm(int cpt, bool collect, int max_maps) {
+  if (collect) {
+    const int nw = collect_warps(cpt, max_maps);
+    const size_t smem = (size_t)nw * collect_warp_smem(cpt, max_maps);
+    if (cpt == 8) return occupancy_of(k_collect_flow<8>, 32 * nw, smem);
+    if (cpt == 4) return occupancy_of(k_collect_flow<4>, 32 * nw, smem);
+    if (cpt == 2) return occupancy_of(k_collect_flow<2>, 32 * nw, smem);
+    return occupancy_of(k_collect_flow<1>, 32 * nw, smem);
+  }
+  if (cpt == 8) return occupancy_of(k_distribute_flow<8>, kThreads, 0);
+  if (cpt == 4) return occupancy_of(k_distribute_flow<4>, kThreads, 0);
+  if (cpt == 2) return occupancy_of(k_distribute_flow<2>, kThreads, 0);
+  return occupancy_of(k_distribute_flow<1>, kThreads, 0);
 }
 
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,

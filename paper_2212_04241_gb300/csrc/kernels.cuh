@@ -25,6 +25,17 @@ struct DevPlan {
   const int32_t *comp_cliques;  // non-root cliques of each component
   const int32_t *comp_roots;    // [n_comp] component root cliques
   const int32_t *pgroup_ptr;    // [n_pgroups + 1] variable groups of the posterior kernel
+  // dataflow schedule: per pass, the items of each flow layer (collect:
+  // deepest layer first; distribute: root first) and the producers a
+  // clique's units wait for on their tile
+  const int64_t *c_flow_pref;   // [n_flow_layers + 1] items before each flow layer
+  const int64_t *c_flow_begin;  // [n_flow_layers] first item of each flow layer
+  const int64_t *d_flow_pref;
+  const int64_t *d_flow_begin;
+  const uint32_t *c_need;       // [n_cliques] collect items of the children that send a message
+  const int32_t *c_notify;      // [n_cliques] parent that receives the clique's message, or -1
+  const uint32_t *d_need;       // [n_cliques] items of the parent's task that writes the clique's ratio
+  int32_t n_flow_layers;
   int32_t n_comp;
   int32_t n_pgroups;
   int32_t n_vars;
@@ -50,6 +61,8 @@ struct DevArena {
   uint32_t *counters;  // [tile][group] pieces finished
   int32_t *ev;         // [tile][var][W] evidence, -1 = unobserved
   int32_t *bad;        // [tile * W] 1 = invalid evidence
+  uint32_t *ready;     // [tile][2][clique] dataflow counters (collect, distribute)
+  unsigned long long *queue;  // dataflow unit counters: [0] collect pass, [16] distribute pass
   uint32_t *errflag;   // one word per arena: nonzero after a bounded device wait expired
   int32_t tiles;       // tiles in this chunk
 };
@@ -70,6 +83,10 @@ constexpr size_t kCollectSmemLimit = 220 * 1024;
 // raise the dynamic shared-memory limit of the collect kernel (once per plan)
 cudaError_t configure_collect_smem(int cpt, size_t bytes);
 constexpr int kMaxTilesPerChunk = 16384;
+// dataflow schedule: one persistent launch per pass (blocks = SMs x resident blocks per SM)
+void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s);
+void launch_distribute_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, cudaStream_t s);
+int flow_blocks_per_sm(int cpt, bool collect, int max_maps);
 
 // plain FP64 path
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,

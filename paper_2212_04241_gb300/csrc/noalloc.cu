@@ -96,9 +96,7 @@ extern "C" jt_status jt_infer_device_noalloc(jt_plan *pl, int32_t n_cases, const
     A.tiles = (nc + W - 1) / W;
     cudaMemsetAsync(A.bad, 0, L.bad * (size_t)A.tiles, s);
     launch_evidence(P.cpt_per_thread, d_ev + b * P.n, nc, pl->dp, A, s);
-    cudaMemsetAsync(A.maxbits, 0, L.maxbits * (size_t)A.tiles, s);
-    for (int lv = P.height; lv >= 0; --lv) enqueue_collect_layer(pl, A, lv, s);
-    for (int lv = 0; lv <= P.height; ++lv) enqueue_distribute_layer(pl, A, lv, s);
+    enqueue_passes(pl, A, s);
     launch_finalize(P.cpt_per_thread, pl->dp, A, nc, P.dcl[P.root].sep_row, d_lp + b, d_post + b * P.sum_card,
                     d_st + b, s);
   }

@@ -12,9 +12,12 @@ namespace jt {
 
 // Bytes of one case tile in each arena region.
 struct ArenaLayout {
-  size_t psi, sep, post, partial, maxbits, counters, ev, bad;
+  size_t psi, sep, post, partial, maxbits, counters, ev, bad, ready;
   size_t per_tile;
-  static constexpr size_t kTail = 256;  // once per arena: the error flag
+  // once per arena: the error flag (offset 0) and the dataflow unit
+  // counters (offsets 64 and 192)
+  static constexpr size_t kTail = 256;
+  static constexpr size_t kQueueOffset = 64;
   size_t bytes(int tiles) const { return per_tile * (size_t)tiles + kTail; }
 };
 
@@ -50,6 +53,8 @@ struct jt_plan {
   cudaStream_t capture_stream = nullptr;  // private stream for graph capture
   void *d_static = nullptr;
   size_t static_bytes = 0;
+  int flow_collect_blocks = 0;            // dataflow grids: SMs x resident blocks per SM
+  int flow_distribute_blocks = 0;
   jt::DevPlan dp{};
   jt::Arena arena;                        // default arena of jt_infer / jt_infer_device
   int budget_tiles_cache = 0;
@@ -70,7 +75,10 @@ jt_status run_chunk(jt_plan *pl, Arena &a, const int32_t *d_ev, int32_t nc, doub
 // bounded wait on this arena; call after synchronising its stream
 jt_status check_arena_flag(Arena &a);
 int budget_tiles(const jt_plan *pl, int64_t budget_bytes);
-// the launch of one tree layer (collect or distribute)
+// the collect and distribute passes of one chunk (after its evidence
+// kernel, before its finalize kernels), in the plan's schedule
+void enqueue_passes(const jt_plan *pl, const DevArena &A, cudaStream_t s);
+// the launch of one tree layer (layer schedule)
 void enqueue_collect_layer(const jt_plan *pl, const DevArena &A, int layer, cudaStream_t s);
 void enqueue_distribute_layer(const jt_plan *pl, const DevArena &A, int layer, cudaStream_t s);
 }  // namespace jt

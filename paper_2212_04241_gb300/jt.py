@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libjt.so")
 JT_OK, JT_EINVAL, JT_ECYCLE, JT_ETOOBIG, JT_ENOMEM, JT_ECUDA, JT_ETIMEOUT, JT_EBUSY, JT_ENOTFOUND = range(9)
 JT_CASE_OK, JT_CASE_ZERO_EVIDENCE, JT_CASE_BAD_EVIDENCE = 0, 1, 2
 JT_ROOT_LARGEST, JT_ROOT_MIN_HEIGHT = 0, 1
+JT_SCHEDULE_DATAFLOW, JT_SCHEDULE_LAYERS = 0, 1
 
 
 class JTError(RuntimeError):
@@ -31,7 +32,8 @@ class CompileOpts(ctypes.Structure):
                 ("cases_per_thread", ctypes.c_int32), ("rows_per_cta", ctypes.c_int32),
                 ("max_clique_entries", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
                 ("use_graphs", ctypes.c_int32), ("items_per_tile", ctypes.c_int32),
-                ("items_per_tile_distribute", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("items_per_tile_distribute", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -145,3 +145,14 @@ def test_evidence_placement_smallest_table(name):
         expect += best[1]
     assert info["separator_evidence_vars"] == expect
     assert expect > 0
+
+
+def test_schedule_option():
+    net = configs.network("bn60")
+    flow = J.Plan(net, host_only=1).info()
+    layers = J.Plan(net, host_only=1, schedule=J.JT_SCHEDULE_LAYERS).info()
+    assert flow["kernels_per_chunk"] == 5          # evidence, two passes, log P(e), posteriors
+    assert layers["kernels_per_chunk"] == 3 + 2 * layers["n_levels"]
+    with pytest.raises(J.JTError) as e:
+        J.Plan(net, host_only=1, schedule=7)
+    assert e.value.status == J.JT_EINVAL

@@ -61,7 +61,7 @@ def test_bn60_full_batch_all_cases():
 
 
 @pytest.mark.parametrize("opts", [dict(cases_per_thread=1), dict(cases_per_thread=2), dict(cases_per_thread=4),
-                                  dict(use_graphs=0), dict(root_rule=J.JT_ROOT_LARGEST),
+                                  dict(use_graphs=0), dict(root_rule=J.JT_ROOT_LARGEST), dict(schedule=J.JT_SCHEDULE_LAYERS),
                                   dict(rows_per_cta=64), dict(rows_per_cta=4096)])
 def test_bn60_option_variants(opts):
     net = configs.network("bn60")
@@ -239,3 +239,19 @@ def test_autotuned_plan_parity():
     assert ns > 0
     p = J.Plan(net, **opts)
     assert_parity32(*p.infer(ev), *_oracle(net, ev), where=f"autotuned {opts}")
+
+
+@pytest.mark.parametrize("name,cpt,n", [("bn60", 1, 333), ("bn60", 4, 1000), ("bn1000", 1, 200), ("bn1000", 4, 700),
+                                        ("bn20", 2, 100), ("bn110", 4, 130)])
+def test_schedules_bitwise_equal(name, cpt, n):
+    """The dataflow schedule (one launch per pass, per-tile readiness
+    counters) computes every case exactly as the layer schedule does: same
+    items, same arithmetic, only the order of independent work differs.  A
+    missing dependency would show as a bitwise difference."""
+    net = configs.network(name)
+    ev = configs.evidence(name, net, n_cases=n, seed=77)
+    a = J.Plan(net, cases_per_thread=cpt, schedule=J.JT_SCHEDULE_DATAFLOW).infer(ev)
+    b = J.Plan(net, cases_per_thread=cpt, schedule=J.JT_SCHEDULE_LAYERS).infer(ev)
+    assert np.array_equal(a[2], b[2])
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1], equal_nan=True)
