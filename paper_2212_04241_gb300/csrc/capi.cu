@@ -265,7 +265,7 @@ static jt_status upload_plan(jt_plan *pl) {
   const size_t o_ci = put(blob, P.citems), o_di = put(blob, P.ditems), o_ip = put(blob, P.ipool);
   const size_t o_b32 = put(blob, P.base32), o_card = put(blob, card32), o_po = put(blob, P.post_off);
   const size_t o_cp = put(blob, P.comp_ptr), o_cv = put(blob, P.comp_vars), o_cc = put(blob, P.comp_cliques);
-  const size_t o_cr = put(blob, P.comp_roots), o_pg = put(blob, P.pgroup_ptr);
+  const size_t o_cr = put(blob, P.comp_roots), o_pg = put(blob, P.pgroup_ptr), o_co = put(blob, P.comp_owner);
   const size_t o_cfp = put(blob, P.c_flow_pref), o_cfb = put(blob, P.c_flow_begin);
   const size_t o_dfp = put(blob, P.d_flow_pref), o_dfb = put(blob, P.d_flow_begin);
   const size_t o_cn = put(blob, P.c_need), o_cno = put(blob, P.c_notify), o_dn = put(blob, P.d_need);
@@ -287,6 +287,8 @@ static jt_status upload_plan(jt_plan *pl) {
   D.comp_vars = reinterpret_cast<const int32_t *>(b + o_cv);
   D.comp_cliques = reinterpret_cast<const int32_t *>(b + o_cc);
   D.comp_roots = reinterpret_cast<const int32_t *>(b + o_cr);
+  D.comp_owner = reinterpret_cast<const int32_t *>(b + o_co);
+  D.n_comp_cliques = (int32_t)P.comp_cliques.size();
   D.n_comp = (int32_t)P.comp_roots.size();
   D.pgroup_ptr = reinterpret_cast<const int32_t *>(b + o_pg);
   D.c_flow_pref = reinterpret_cast<const int64_t *>(b + o_cfp);
@@ -314,6 +316,11 @@ static jt_status upload_plan(jt_plan *pl) {
     return JT_ETOOBIG;
   }
   JT_CUDA_TRY(configure_collect_smem(P.cpt_per_thread, smem));
+  if (logpe_smem_bytes((int)P.comp_roots.size()) > 220 * 1024) {
+    set_error("the network splits into too many independent component trees for the log P(e) kernel");
+    return JT_ETOOBIG;
+  }
+  JT_CUDA_TRY(configure_logpe_smem((int)P.comp_roots.size()));
   int sms = 0;
   JT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
   pl->flow_collect_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, true, max_maps);

@@ -811,6 +811,12 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       P.comp_cliques.insert(P.comp_cliques.end(), cliques_of[c].begin(), cliques_of[c].end());
       P.dcl[c].comp_end = (int32_t)P.comp_cliques.size();
     }
+    // component (index into comp_roots) of each comp_cliques entry
+    P.comp_owner.assign(P.comp_cliques.size(), 0);
+    for (size_t q = 0; q < P.comp_roots.size(); ++q) {
+      const DClique &D = P.dcl[P.comp_roots[q]];
+      for (int k = D.comp_begin; k < D.comp_end; ++k) P.comp_owner[k] = (int32_t)q;
+    }
   }
 
   // ---------------------------------------------------------------------

@@ -210,22 +210,31 @@ __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) 
 // ---------------------------------------------------------------------------
 // evidence: [case][var] -> [tile][var][W], invalid states flagged
 // ---------------------------------------------------------------------------
-__global__ void k_evidence(const int32_t *__restrict__ ev_in, int32_t n_cases, DevPlan P,
-                           DevArena A, int W) {
-  const int64_t total = (int64_t)A.tiles * W * P.n_vars;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = i / P.n_vars;
-    const int v = (int)(i - c * P.n_vars);
+// A block moves 32 cases x 32 variables through shared memory, so both the
+// [case][var] reads and the [tile][var][W] writes are coalesced.  Cases of
+// the chunk's last tile beyond n_cases get -1 (unobserved).
+__global__ void k_evidence(const int32_t *__restrict__ ev_in, int32_t n_cases, DevPlan P, DevArena A, int W) {
+  __shared__ int32_t t[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32;
+  const int v0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i;
+    const int v = v0 + threadIdx.x;
     int val = -1;
-    if (c < n_cases) {
+    if (v < P.n_vars && c < n_cases) {
       val = ev_in[c * P.n_vars + v];
       if (val < -1 || val >= P.card[v]) {
         A.bad[c] = 1;
         val = -1;
       }
     }
-    A.ev[((c / W) * P.n_vars + v) * W + (c % W)] = val;
+    t[i][threadIdx.x] = val;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int v = v0 + j;
+    const int64_t c = c0 + threadIdx.x;
+    if (v < P.n_vars && c < (int64_t)A.tiles * W) A.ev[((c / W) * P.n_vars + v) * W + (c % W)] = t[threadIdx.x][j];
   }
 }
 
@@ -683,49 +692,62 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
 // ---------------------------------------------------------------------------
 constexpr int kStageCols = 16;
 
-constexpr int kLogpeSlices = 4;  // thread rows of a k_logpe block, each over a share of the components
+// k_logpe: a block holds 32 cases x kLogpeSlices slices.  Phase 1 finds,
+// per case, the components holding an observed variable (a bitmask per
+// component in shared memory); phase 2 spreads every observed component's
+// terms -- the root total's log and base exponent, the other cliques'
+// message exponents -- over the slices; a fixed-order sum over the slices
+// gives each case's log P(e).
+constexpr int kLogpeSlices = 32;
 
 __global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *__restrict__ log_pe,
                         int32_t *__restrict__ status) {
-  __shared__ double s_lz[kLogpeSlices][256];
-  __shared__ long long s_K[kLogpeSlices][256];
-  __shared__ int s_zero[kLogpeSlices][256];
-  const int tile = blockIdx.x;
-  const int c = threadIdx.x;      // case within the tile
-  const int slice = threadIdx.y;  // share of the component roots
-  const int64_t cs = (int64_t)tile * W + c;
-  // Messages multiplied into a parent were scaled by 2^-k: add k back.
-  // Every component root contributes the log of its total -- except a
-  // component without any observed variable, whose probability is exactly 1
-  // (a sum over all states of a product of CPTs) and contributes 0.
-  long long K = 0;
-  double lz = 0.0;
-  int zero = 0;
-  for (int q = 0; q < P.n_comp; ++q) {
+  extern __shared__ unsigned char logpe_smem[];
+  double *s_lz = reinterpret_cast<double *>(logpe_smem);              // [slice][32]
+  long long *s_K = reinterpret_cast<long long *>(s_lz + kLogpeSlices * 32);
+  int *s_zero = reinterpret_cast<int *>(s_K + kLogpeSlices * 32);
+  unsigned *s_obs = reinterpret_cast<unsigned *>(s_zero + kLogpeSlices * 32);  // [n_comp], bit c = case c
+  const int c = threadIdx.x;      // case within the block
+  const int slice = threadIdx.y;
+  const int64_t cs = (int64_t)blockIdx.x * 32 + c;
+  const int tile = (int)(cs / W), col = (int)(cs - (int64_t)tile * W);
+  for (int q = slice * 32 + c; q < P.n_comp; q += 32 * kLogpeSlices) s_obs[q] = 0u;
+  __syncthreads();
+  // phase 1: components with an observed variable (a component without one
+  // has probability exactly 1: a sum over all states of a product of CPTs)
+  for (int q = slice; q < P.n_comp; q += kLogpeSlices) {
     const int cl = P.comp_roots[q];
     bool observed = false;
     for (int k = P.comp_ptr[cl]; k < P.comp_ptr[cl + 1] && !observed; ++k)
-      observed = A.ev[((int64_t)tile * P.n_vars + P.comp_vars[k]) * W + c] >= 0;
-    if (!observed) continue;
-    const DClique &D = P.cl[cl];
-    if (q % kLogpeSlices == slice) {
-      const float z = A.phistar[((int64_t)tile * P.sep_rows + D.sep_row) * W + c];
-      if (z > 0.f) lz += log((double)z); else zero = 1;
-      K += D.comp_base_exp;
-    }
-    // the component's other cliques, shared among the slices
-    for (int k = D.comp_begin + slice; k < D.comp_end; k += kLogpeSlices)
-      K += pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + P.comp_cliques[k]) * W + c]);
+      observed = A.ev[((int64_t)tile * P.n_vars + P.comp_vars[k]) * W + col] >= 0;
+    if (observed) atomicOr(&s_obs[q], 1u << c);
   }
-  s_lz[slice][c] = lz;
-  s_K[slice][c] = K;
-  s_zero[slice][c] = zero;
+  __syncthreads();
+  // phase 2: messages multiplied into a parent were scaled by 2^-k, so k is
+  // added back; every observed component root adds the log of its total
+  long long K = 0;
+  double lz = 0.0;
+  int zero = 0;
+  for (int q = slice; q < P.n_comp; q += kLogpeSlices) {
+    if (!((s_obs[q] >> c) & 1u)) continue;
+    const DClique &D = P.cl[P.comp_roots[q]];
+    const float z = A.phistar[((int64_t)tile * P.sep_rows + D.sep_row) * W + col];
+    if (z > 0.f) lz += log((double)z); else zero = 1;
+    K += D.comp_base_exp;
+  }
+  for (int k = slice; k < P.n_comp_cliques; k += kLogpeSlices) {
+    if (!((s_obs[P.comp_owner[k]] >> c) & 1u)) continue;
+    K += pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + P.comp_cliques[k]) * W + col]);
+  }
+  s_lz[slice * 32 + c] = lz;
+  s_K[slice * 32 + c] = K;
+  s_zero[slice * 32 + c] = zero;
   __syncthreads();
   if (slice != 0 || cs >= n_cases) return;
   for (int t = 1; t < kLogpeSlices; ++t) {
-    lz += s_lz[t][c];
-    K += s_K[t][c];
-    zero |= s_zero[t][c];
+    lz += s_lz[t * 32 + c];
+    K += s_K[t * 32 + c];
+    zero |= s_zero[t * 32 + c];
   }
   const int bad = A.bad[cs];
   const int st = bad ? JT_CASE_BAD_EVIDENCE : (zero ? JT_CASE_ZERO_EVIDENCE : JT_CASE_OK);
@@ -737,11 +759,6 @@ __global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *_
   status[cs] = st;
 }
 
-// ---------------------------------------------------------------------------
-// finalize, part 2: FP64 posterior normalisation.  Block (tile, variable
-// group), one thread per case; values are staged in shared memory and
-// written out row by row so that global writes are contiguous.
-// ---------------------------------------------------------------------------
 __global__ void k_posterior(DevPlan P, DevArena A, int W, int32_t n_cases, const int32_t *__restrict__ status,
                             double *__restrict__ post) {
   extern __shared__ double stage[];  // [W][kStageCols + 1]
@@ -766,9 +783,12 @@ __global__ void k_posterior(DevPlan P, DevArena A, int W, int32_t n_cases, const
     const int r = P.card[v];
     const int ev = A.ev[((int64_t)tile * P.n_vars + v) * W + c];
     const float *m = A.post + ((int64_t)tile * P.post_rows + off) * W + c;
+    // FP64 sum and one FP64 reciprocal per variable (FP64 division is slow
+    // on this part; m * (1/s) differs from m / s by at most an FP64 ulp)
     double s = 0.0;
     if (st == JT_CASE_OK && ev < 0)
       for (int j = 0; j < r; ++j) s += (double)m[(int64_t)j * W];
+    const double inv = 1.0 / s;
     for (int j = 0; j < r; ++j) {
       if (off + j - col0 == kStageCols) {
         flush(kStageCols);
@@ -777,7 +797,7 @@ __global__ void k_posterior(DevPlan P, DevArena A, int W, int32_t n_cases, const
       double val;
       if (st != JT_CASE_OK) val = NAN;
       else if (ev >= 0) val = (j == ev) ? 1.0 : 0.0;
-      else val = (double)m[(int64_t)j * W] / s;
+      else val = (double)m[(int64_t)j * W] * inv;
       stage[c * (kStageCols + 1) + (off + j - col0)] = val;
     }
   }
@@ -862,9 +882,8 @@ size_t collect_warp_smem_bytes(int cpt, int max_maps) { return collect_warp_smem
 void launch_evidence(int cpt, const int32_t *d_ev_in, int32_t n_cases, const DevPlan &P,
                      const DevArena &A, cudaStream_t s) {
   const int W = 32 * cpt;
-  const int64_t total = (int64_t)A.tiles * W * P.n_vars;
-  unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(total, 256), 152 * 16);
-  k_evidence<<<blocks, 256, 0, s>>>(d_ev_in, n_cases, P, A, W);
+  const dim3 grid((unsigned)(((int64_t)A.tiles * W + 31) / 32), (unsigned)((P.n_vars + 31) / 32));
+  k_evidence<<<grid, dim3(32, 8), 0, s>>>(d_ev_in, n_cases, P, A, W);
 }
 
 // Warps per collect block: eight, fewer when a layer's cliques carry so many
@@ -982,6 +1001,17 @@ void launch_plain_finalize(const double *pe, const double *marg, const int32_t *
   k_plain_finalize<<<1, 256, 0, s>>>(pe, marg, d_ev, card, post_off, n_vars, d_log_pe, d_post, d_status);
 }
 
+size_t logpe_smem_bytes(int n_comp) {
+  return (sizeof(double) + sizeof(long long) + sizeof(int)) * kLogpeSlices * 32 +
+         sizeof(unsigned) * (size_t)std::max(1, n_comp);
+}
+
+cudaError_t configure_logpe_smem(int n_comp) {
+  const size_t bytes = logpe_smem_bytes(n_comp);
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_logpe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cases,
                      int64_t root_sep_row, double *d_log_pe, double *d_post, int32_t *d_status,
                      cudaStream_t s) {
@@ -989,7 +1019,8 @@ void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cas
   if (n_cases <= 0) return;
   const int W = 32 * cpt;
   const unsigned tiles = (unsigned)((n_cases + W - 1) / W);
-  k_logpe<<<tiles, dim3(W, kLogpeSlices), 0, s>>>(P, A, W, n_cases, d_log_pe, d_status);
+  const size_t lsmem = logpe_smem_bytes(P.n_comp);
+  k_logpe<<<(unsigned)((n_cases + 31) / 32), dim3(32, kLogpeSlices), lsmem, s>>>(P, A, W, n_cases, d_log_pe, d_status);
   const size_t smem = sizeof(double) * (size_t)W * (kStageCols + 1);
   k_posterior<<<dim3(tiles, (unsigned)P.n_pgroups), W, smem, s>>>(P, A, W, n_cases, d_status, d_post);
 }

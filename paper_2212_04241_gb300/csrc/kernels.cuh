@@ -24,6 +24,8 @@ struct DevPlan {
   const int32_t *comp_vars;  // [n]
   const int32_t *comp_cliques;  // non-root cliques of each component
   const int32_t *comp_roots;    // [n_comp] component root cliques
+  const int32_t *comp_owner;    // per comp_cliques entry: its component
+  int32_t n_comp_cliques;       // entries of comp_cliques
   const int32_t *pgroup_ptr;    // [n_pgroups + 1] variable groups of the posterior kernel
   // dataflow schedule: per pass, the items of each flow layer (collect:
   // deepest layer first; distribute: root first) and the producers a
@@ -82,6 +84,9 @@ size_t collect_warp_smem_bytes(int cpt, int max_maps);   // one warp
 constexpr size_t kCollectSmemLimit = 220 * 1024;
 // raise the dynamic shared-memory limit of the collect kernel (once per plan)
 cudaError_t configure_collect_smem(int cpt, size_t bytes);
+// the log P(e) kernel keeps one word per component tree in shared memory
+size_t logpe_smem_bytes(int n_comp);
+cudaError_t configure_logpe_smem(int n_comp);
 constexpr int kMaxTilesPerChunk = 16384;
 // dataflow schedule: one persistent launch per pass (blocks = SMs x resident blocks per SM)
 void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s);
