@@ -45,6 +45,20 @@ WORKLOADS = {
 DEFAULT_CASES = {"bn20": 100, "bn60": 4096, "bn110": 8192, "bn420": 1024, "bn1000": 4096}
 
 
+# DRAM traffic of the dominant kernel per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the full-size workload), valid
+# only for the kernel source it was taken with: keyed by (workload, cases,
+# sha256 prefix of csrc/kernels.cu); any other source reports null.
+MEASURED_TRAFFIC = {}
+
+
+def _kernel_source_hash():
+    import hashlib
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2212_04241_gb300", "csrc", "kernels.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -259,6 +273,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix latency measurement")
     ap.add_argument("--no-autotune", action="store_true", help="default plan options instead of jt_autotune")
+    ap.add_argument("--plan", default="", help="fixed plan options as JSON (e.g. '{\"items_per_tile\": 96}'), "
+                    "instead of jt_autotune")
     ap.add_argument("--serving-only", action="store_true", help="only the serving-mix measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -289,7 +305,10 @@ def main():
 
     import paper_2212_04241_gb300.jt as J
     # the library's autotuner picks the tile shape for this network and batch
-    tuned, _ = J.autotune(net, n_cases) if not args.no_autotune else ({}, None)
+    if args.plan:
+        tuned = json.loads(args.plan)
+    else:
+        tuned, _ = J.autotune(net, n_cases) if not args.no_autotune else ({}, None)
     plan = J.Plan(net, **tuned)
     stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
@@ -363,9 +382,12 @@ def main():
     bytes_dom = per_case * n_cases
     achieved = bytes_dom / (kinds[dom] / 1e3) / 1e9
     peak, peak_src = _peaks()
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+    dataflow = int(tuned.get("schedule", J.JT_SCHEDULE_DATAFLOW)) == J.JT_SCHEDULE_DATAFLOW
+    kernel = f"k_{dom}_flow" if dataflow else f"k_{dom}"
+    traffic = MEASURED_TRAFFIC.get((name, n_cases, _kernel_source_hash())) if dataflow else None
+    roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "launches": prof[f"{dom}_launches"],
+                "traffic": traffic, "launches": prof[f"{dom}_launches"],
                 "kernel_ms_per_pass": kinds[dom], "other_kernel_ms_per_pass": kinds["collect" if dom == "distribute" else "distribute"],
                 "whole_pass_algorithmic_GBps": info["algorithmic_bytes_per_case"] * n_cases / (prof["total_ms"] / 1e3) / 1e9}
 
@@ -373,12 +395,17 @@ def main():
     e2e = None
     if rank == 0:
         import torch as _t
+        # page-locked host buffers (allocated once, outside the timed region):
+        # every step copies the evidence in and all outputs back
         ev_pinned = _t.from_numpy(ev).pin_memory().numpy()
-        plan.infer(ev_pinned)
+        out = (_t.empty(n_cases, dtype=_t.float64, pin_memory=True).numpy(),
+               _t.empty((n_cases, plan.sum_card), dtype=_t.float64, pin_memory=True).numpy(),
+               _t.empty(n_cases, dtype=_t.int32, pin_memory=True).numpy())
+        plan.infer(ev_pinned, out=out)
         reps = max(3, min(args.steps, 10))
         t0 = time.perf_counter()
         for _ in range(reps):
-            plan.infer(ev_pinned)
+            plan.infer(ev_pinned, out=out)
         dt = (time.perf_counter() - t0) / reps
         e2e = {"value": n_cases / dt, "unit": "cases/s", "h2d_bytes_per_step": int(ev.nbytes),
                "d2h_bytes_per_step": int(n_cases * (8 + 8 * plan.sum_card + 4)), "ms_per_step": dt * 1e3}
@@ -416,7 +443,10 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[name], "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
                    "chunk_cases": info["chunk_cases"], "levels": info["n_levels"],
-                   "autotuned": {k: tuned[k] for k in ("cases_per_thread", "items_per_tile", "items_per_tile_distribute")} if tuned else None,
+                   "autotuned": ({k: tuned[k] for k in ("cases_per_thread", "items_per_tile", "items_per_tile_distribute")}
+                                 if tuned and not args.plan else None),
+                   "plan_options": tuned if args.plan else None,
+                   "schedule": "dataflow" if dataflow else "layers",
                    "sum_clique_entries": info["sum_clique_entries"],
                    "l2": "inputs larger than L2 (psi arena %.2f GB per step)" % (4.0 * info["sum_clique_entries"] * n_cases / 1e9),
                    "parallelism": f"cases sharded, {world} rank(s)"},

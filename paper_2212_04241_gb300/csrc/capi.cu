@@ -524,6 +524,31 @@ extern "C" jt_status jt_infer(jt_plan *pl, int32_t n_cases, const int32_t *ev, d
   double *h_po = reinterpret_cast<double *>(h + pl->io_ev + pl->io_lp);
   int32_t *d_st = reinterpret_cast<int32_t *>(d + pl->io_ev + pl->io_lp + pl->io_post);
   int32_t *h_st = reinterpret_cast<int32_t *>(h + pl->io_ev + pl->io_lp + pl->io_post);
+  // Page-locked caller buffers are copied directly (asynchronously, one
+  // synchronisation at the end); pageable ones through the plan's pinned
+  // staging buffer.
+  auto pinned = [](const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+  };
+  if (pinned(ev) && pinned(lp) && pinned(post) && pinned(cst)) {
+    for (int64_t b = 0; b < n_cases; b += chunk) {
+      const int32_t nc = (int32_t)std::min<int64_t>(chunk, n_cases - b);
+      JT_CUDA_TRY(cudaMemcpyAsync(d_ev, ev + b * P.n, sizeof(int32_t) * (size_t)nc * P.n, cudaMemcpyHostToDevice, s));
+      st = run_chunk(pl, pl->arena, d_ev, nc, d_lp, d_po, d_st, s);
+      if (st != JT_OK) return st;
+      JT_CUDA_TRY(cudaMemcpyAsync(lp + b, d_lp, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+      JT_CUDA_TRY(cudaMemcpyAsync(post + b * P.sum_card, d_po, sizeof(double) * (size_t)nc * P.sum_card,
+                                  cudaMemcpyDeviceToHost, s));
+      JT_CUDA_TRY(cudaMemcpyAsync(cst + b, d_st, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, s));
+    }
+    JT_CUDA_TRY(cudaStreamSynchronize(s));
+    return check_arena_flag(pl->arena);
+  }
   for (int64_t b = 0; b < n_cases; b += chunk) {
     const int32_t nc = (int32_t)std::min<int64_t>(chunk, n_cases - b);
     std::memcpy(h_ev, ev + b * P.n, sizeof(int32_t) * (size_t)nc * P.n);

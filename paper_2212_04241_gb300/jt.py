@@ -137,7 +137,7 @@ def autotune(net, n_cases: int, **opts):
                            int(n_cases), ctypes.byref(best), ctypes.byref(ns)))
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
                                            "items_per_tile_distribute", "use_graphs", "arena_bytes",
-                                           "max_clique_entries")}
+                                           "max_clique_entries", "schedule")}
     return out, ns.value
 
 
@@ -190,11 +190,21 @@ class Plan:
         return (np.zeros(m, dtype=np.float64), np.zeros((m, self.sum_card), dtype=np.float64),
                 np.zeros(m, dtype=np.int32))
 
-    def infer(self, evidence, stream=None):
-        """Batched FP32 path, host buffers (jt_infer)."""
+    def infer(self, evidence, stream=None, out=None):
+        """Batched FP32 path, host buffers (jt_infer).  ``out`` = (log_pe,
+        posteriors, status) preallocated C-contiguous arrays of float64 [n],
+        float64 [n, sum_card] and int32 [n]; page-locked ones are copied to
+        and from the device directly."""
         ev = np.ascontiguousarray(np.atleast_2d(evidence), dtype=np.int32)
         assert ev.shape[1] == self.n
-        lp, post, st = self._outputs(ev.shape[0])
+        if out is None:
+            lp, post, st = self._outputs(ev.shape[0])
+        else:
+            lp, post, st = out
+            m = ev.shape[0]
+            assert lp.dtype == np.float64 and lp.shape == (m,) and lp.flags.c_contiguous
+            assert post.dtype == np.float64 and post.shape == (m, self.sum_card) and post.flags.c_contiguous
+            assert st.dtype == np.int32 and st.shape == (m,) and st.flags.c_contiguous
         _check(lib.jt_infer(self._h, ev.shape[0], _ptr(ev), _ptr(lp), _ptr(post), _ptr(st), stream))
         return lp, post, st
 

@@ -96,6 +96,27 @@ def test_device_path_matches_host_path_bitwise():
     assert np.array_equal(d_st.cpu().numpy(), st)
 
 
+@pytest.mark.parametrize("chunks", [1, 4])
+def test_pinned_host_buffers_match_pageable_bitwise(chunks):
+    """jt_infer copies page-locked caller buffers directly (asynchronously,
+    over every chunk); the results equal the staged pageable path bit for bit."""
+    net = configs.network("bn60")
+    ev = configs.evidence("bn60", net, n_cases=1000)
+    opts = {}
+    if chunks > 1:
+        probe = J.Plan(net)
+        probe.infer(ev[:1])
+        opts = dict(arena_bytes=2 * probe.info()["arena_bytes"])   # 1000 cases in 4 chunks of 256
+    p = J.Plan(net, **opts)
+    lp, post, st = p.infer(ev)
+    ev_pin = torch.from_numpy(ev).pin_memory().numpy()
+    out = (torch.full((1000,), -7.0, dtype=torch.float64, pin_memory=True).numpy(),
+           torch.full((1000, p.sum_card), -7.0, dtype=torch.float64, pin_memory=True).numpy(),
+           torch.full((1000,), -7, dtype=torch.int32, pin_memory=True).numpy())
+    p.infer(ev_pin, out=out)
+    assert np.array_equal(out[0], lp) and np.array_equal(out[1], post) and np.array_equal(out[2], st)
+
+
 def test_result_independent_of_batch_position():
     """A case gives bit-identical results alone, in a small batch and at any
     position of a large batch (fixed per-case reduction order)."""
