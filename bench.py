@@ -46,10 +46,15 @@ DEFAULT_CASES = {"bn20": 100, "bn60": 4096, "bn110": 8192, "bn420": 1024, "bn100
 
 
 # DRAM traffic of the dominant kernel per launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the full-size workload), valid
-# only for the kernel source it was taken with: keyed by (workload, cases,
-# sha256 prefix of csrc/kernels.cu); any other source reports null.
-MEASURED_TRAFFIC = {}
+# dram__bytes_write.sum from one ncu capture of the full-size workload,
+# profiles/dram_traffic_dataflow_bn60_B4096.md), valid only for the plan
+# shape and kernel source it was taken with: keyed by (workload, cases,
+# items_per_tile_distribute, sha256 prefix of csrc/kernels.cu); anything
+# else reports null.
+MEASURED_TRAFFIC = {
+    ("bn60", 4096, 192, "e34255e21b9897a2"): 2080317440,
+    ("bn60", 4096, 384, "e34255e21b9897a2"): 2057050624,
+}
 
 
 def _kernel_source_hash():
@@ -384,7 +389,10 @@ def main():
     peak, peak_src = _peaks()
     dataflow = int(tuned.get("schedule", J.JT_SCHEDULE_DATAFLOW)) == J.JT_SCHEDULE_DATAFLOW
     kernel = f"k_{dom}_flow" if dataflow else f"k_{dom}"
-    traffic = MEASURED_TRAFFIC.get((name, n_cases, _kernel_source_hash())) if dataflow else None
+    # the plan's distribute work-item target (0 in the options = items_per_tile, whose 0 = 192)
+    items_d = int(tuned.get("items_per_tile_distribute") or tuned.get("items_per_tile") or 192)
+    traffic = (MEASURED_TRAFFIC.get((name, n_cases, items_d, _kernel_source_hash()))
+               if dataflow and dom == "distribute" else None)
     roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "launches": prof[f"{dom}_launches"],
