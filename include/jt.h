@@ -69,7 +69,10 @@ typedef enum {
 enum {
   JT_CASE_OK = 0,
   JT_CASE_ZERO_EVIDENCE = 1, /* P(e) = 0: log_pe = -inf, posteriors NaN */
-  JT_CASE_BAD_EVIDENCE = 2   /* a state outside [-1, card-1]: outputs NaN */
+  JT_CASE_BAD_EVIDENCE = 2,  /* a state outside [-1, card-1]: outputs NaN */
+  JT_CASE_INCOMPLETE = 3     /* a bounded device wait of the pass expired:
+                                outputs NaN (the call, or the next
+                                synchronous one, returns JT_ETIMEOUT) */
 };
 
 enum {
@@ -112,7 +115,15 @@ typedef struct {
                                  0 = items_per_tile */
   int32_t schedule;           /* JT_SCHEDULE_*: how the work of a pass is
                                  ordered on the GPU (default dataflow) */
-  int32_t reserved[4];
+  int32_t wait_limit_us;      /* dataflow schedule: bound of a device wait
+                                 for producers on the same tile; when it
+                                 expires the call returns JT_ETIMEOUT;
+                                 0 = automatic (2 s) */
+  int32_t stall_clique;       /* testing only: 0 (default) = off; k > 0 makes
+                                 the collect work of clique k-1 wait for one
+                                 producer more than exists, so its waits
+                                 expire (exercises JT_ETIMEOUT) */
+  int32_t reserved[2];
 } jt_compile_opts;
 
 typedef struct {
@@ -166,6 +177,11 @@ JT_API jt_status jt_compile(int32_t n_vars, const int32_t *card, const int32_t *
  * posterior normalisation), and copies the results back; the call returns
  * after the results are in the caller's buffers.  cuda_stream is a
  * cudaStream_t or NULL for the plan's own stream.  Any n_cases >= 0.
+ * Page-locked (pinned) caller buffers are copied directly and
+ * asynchronously; pageable ones through the plan's pinned staging buffer.
+ * Returns JT_ETIMEOUT if a bounded device wait expired (the dataflow
+ * schedule's waits for producers, limit wait_limit_us); the condition is
+ * then cleared.
  */
 JT_API jt_status jt_infer(jt_plan *plan, int32_t n_cases, const int32_t *evidence, double *log_pe,
                    double *posteriors, int32_t *case_status, void *cuda_stream);
@@ -175,7 +191,10 @@ JT_API jt_status jt_infer(jt_plan *plan, int32_t n_cases, const int32_t *evidenc
  * device).  Work is enqueued on cuda_stream (NULL = the plan's stream) and
  * the call returns without synchronising; the outputs are valid once the
  * stream has reached that point.  Evidence states outside [-1, card-1] give
- * JT_CASE_BAD_EVIDENCE for that case only.
+ * JT_CASE_BAD_EVIDENCE for that case only.  An expired device wait marks
+ * every case of the call JT_CASE_INCOMPLETE (outputs NaN); the condition
+ * stays set (later device calls are marked the same) until a synchronous
+ * call (jt_infer, jt_profile) returns JT_ETIMEOUT and clears it.
  */
 JT_API jt_status jt_infer_device(jt_plan *plan, int32_t n_cases, const int32_t *d_evidence,
                           double *d_log_pe, double *d_posteriors, int32_t *d_case_status,

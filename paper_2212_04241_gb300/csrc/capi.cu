@@ -200,7 +200,7 @@ jt_status check_arena_flag(Arena &a) {
   JT_CUDA_TRY(cudaMemcpy(&f, a.da.errflag, sizeof(f), cudaMemcpyDeviceToHost));
   if (f) {
     cudaMemset(a.da.errflag, 0, sizeof(uint32_t));
-    set_error("a bounded device wait expired (TMA copy not completed)");
+    set_error("a bounded device wait for work on the same case tile expired");
     return JT_ETIMEOUT;
   }
   return JT_OK;
@@ -299,6 +299,7 @@ static jt_status upload_plan(jt_plan *pl) {
   D.c_notify = reinterpret_cast<const int32_t *>(b + o_cno);
   D.d_need = reinterpret_cast<const uint32_t *>(b + o_dn);
   D.n_flow_layers = P.height + 1;
+  D.wait_limit_ns = 1000ull * (uint64_t)(P.opts.wait_limit_us > 0 ? P.opts.wait_limit_us : 2000000);
   D.n_pgroups = (int32_t)P.pgroup_ptr.size() - 1;
   D.n_vars = P.n;
   D.n_cliques = (int32_t)P.cl.size();

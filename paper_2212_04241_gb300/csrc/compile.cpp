@@ -766,6 +766,13 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     const DTask &T = P.dtask[it.task];
     if (T.kind == TASK_CHILD) ++P.d_need[T.dst];
   }
+  if (opts.stall_clique > 0) {
+    if (opts.stall_clique > m) {
+      err = "stall_clique out of range";
+      return JT_EINVAL;
+    }
+    ++P.c_need[opts.stall_clique - 1];  // a producer that never comes
+  }
 
   P.base_exp_sum = 0;
   for (int c = 0; c < m; ++c) P.base_exp_sum += base_exp[c];

@@ -582,9 +582,8 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
 // A unit only waits for units taken before it, and every taken unit is held
 // by a running warp, so the pass always completes.  Waits are bounded: a
 // wait that runs out sets the arena's error flag, every other wait then
-// gives up at once, and the host reports JT_ETIMEOUT.
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
-
+// gives up at once, and the host reports JT_ETIMEOUT (limit: the plan's
+// wait_limit_us, 2 s by default).
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -594,7 +593,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Lane 0 waits until *ctr >= need and fences (acquire: the producers'
 // writes made before their counter increments are visible to it); the warp
 // barrier then orders those writes before every lane's later loads.
-__device__ __forceinline__ bool wait_ready(const uint32_t *ctr, uint32_t need, uint32_t *errflag, int lane) {
+__device__ __forceinline__ bool wait_ready(const uint32_t *ctr, uint32_t need, uint32_t *errflag, uint64_t limit_ns,
+                                           int lane) {
   int ok = 1;
   if (lane == 0) {
     const volatile uint32_t *vc = ctr;
@@ -604,7 +604,7 @@ __device__ __forceinline__ bool wait_ready(const uint32_t *ctr, uint32_t need, u
       unsigned ns = 32;
       while (*vc < need) {
         if (*ve != 0u) { ok = 0; break; }
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit_ns) {
           atomicOr(errflag, 1u);
           ok = 0;
           break;
@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect_flow(
     const DItem it = P.citems[item];
     uint32_t *ready = A.ready + (int64_t)tile * 2 * P.n_cliques;
     const uint32_t need = P.c_need[it.task];
-    if (need == 0u || wait_ready(ready + it.task, need, A.errflag, lane))
+    if (need == 0u || wait_ready(ready + it.task, need, A.errflag, P.wait_limit_ns, lane))
       collect_item<CPT, LD_PLAIN>(P, A, it, tile, ws, max_maps, lane);
     const int parent = P.c_notify[it.task];
     signal_done(parent >= 0 ? ready + parent : nullptr, lane);
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
     const DTask &T = P.tasks[it.task];
     uint32_t *ready = A.ready + ((int64_t)tile * 2 + 1) * P.n_cliques;
     const uint32_t need = P.d_need[T.clique];
-    if (need == 0u || wait_ready(ready + T.clique, need, A.errflag, lane))
+    if (need == 0u || wait_ready(ready + T.clique, need, A.errflag, P.wait_limit_ns, lane))
       distribute_item<CPT, LD_PLAIN>(P, A, it, tile, lane);
     signal_done(T.kind == TASK_CHILD ? ready + T.dst : nullptr, lane);
   }
@@ -750,7 +750,9 @@ __global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *_
     zero |= s_zero[t * 32 + c];
   }
   const int bad = A.bad[cs];
-  const int st = bad ? JT_CASE_BAD_EVIDENCE : (zero ? JT_CASE_ZERO_EVIDENCE : JT_CASE_OK);
+  const bool incomplete = *reinterpret_cast<volatile const uint32_t *>(A.errflag) != 0u;
+  const int st = incomplete ? JT_CASE_INCOMPLETE
+                            : bad ? JT_CASE_BAD_EVIDENCE : (zero ? JT_CASE_ZERO_EVIDENCE : JT_CASE_OK);
   double lp;
   if (st == JT_CASE_OK) lp = lz + (double)K * 0.69314718055994530942;
   else if (st == JT_CASE_ZERO_EVIDENCE) lp = -INFINITY;

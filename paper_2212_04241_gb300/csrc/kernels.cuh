@@ -38,6 +38,7 @@ struct DevPlan {
   const int32_t *c_notify;      // [n_cliques] parent that receives the clique's message, or -1
   const uint32_t *d_need;       // [n_cliques] items of the parent's task that writes the clique's ratio
   int32_t n_flow_layers;
+  uint64_t wait_limit_ns;       // bound of a dataflow wait
   int32_t n_comp;
   int32_t n_pgroups;
   int32_t n_vars;

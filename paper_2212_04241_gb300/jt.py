@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libjt.so")
 
 JT_OK, JT_EINVAL, JT_ECYCLE, JT_ETOOBIG, JT_ENOMEM, JT_ECUDA, JT_ETIMEOUT, JT_EBUSY, JT_ENOTFOUND = range(9)
-JT_CASE_OK, JT_CASE_ZERO_EVIDENCE, JT_CASE_BAD_EVIDENCE = 0, 1, 2
+JT_CASE_OK, JT_CASE_ZERO_EVIDENCE, JT_CASE_BAD_EVIDENCE, JT_CASE_INCOMPLETE = 0, 1, 2, 3
 JT_ROOT_LARGEST, JT_ROOT_MIN_HEIGHT = 0, 1
 JT_SCHEDULE_DATAFLOW, JT_SCHEDULE_LAYERS = 0, 1
 
@@ -33,7 +33,8 @@ class CompileOpts(ctypes.Structure):
                 ("max_clique_entries", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
                 ("use_graphs", ctypes.c_int32), ("items_per_tile", ctypes.c_int32),
                 ("items_per_tile_distribute", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("wait_limit_us", ctypes.c_int32), ("stall_clique", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):

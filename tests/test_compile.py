@@ -156,3 +156,6 @@ def test_schedule_option():
     with pytest.raises(J.JTError) as e:
         J.Plan(net, host_only=1, schedule=7)
     assert e.value.status == J.JT_EINVAL
+    with pytest.raises(J.JTError) as e:
+        J.Plan(net, host_only=1, stall_clique=layers["n_cliques"] + 1)
+    assert e.value.status == J.JT_EINVAL

@@ -276,3 +276,30 @@ def test_schedules_bitwise_equal(name, cpt, n):
     assert np.array_equal(a[2], b[2])
     assert np.array_equal(a[0], b[0])
     assert np.array_equal(a[1], b[1], equal_nan=True)
+
+
+def test_expired_wait_reports_timeout_and_context_stays_usable():
+    """A dataflow wait that can never be satisfied (a producer that does not
+    exist, set by the testing option stall_clique) expires after the plan's
+    wait limit: the call returns JT_ETIMEOUT, the device path marks every
+    case JT_CASE_INCOMPLETE, and other plans keep working on the device."""
+    import time
+    net = configs.network("bn60")
+    ev = configs.evidence("bn60", net, n_cases=300)
+    good = J.Plan(net)
+    root = good.info()["root"]
+    bad = J.Plan(net, stall_clique=root + 1, wait_limit_us=2000)
+    t0 = time.time()
+    with pytest.raises(J.JTError) as e:
+        bad.infer(ev)
+    assert e.value.status == J.JT_ETIMEOUT
+    assert time.time() - t0 < 10
+    d_ev = torch.from_numpy(ev).cuda()
+    d_lp = torch.empty(300, dtype=torch.float64, device="cuda")
+    d_post = torch.empty((300, bad.sum_card), dtype=torch.float64, device="cuda")
+    d_st = torch.empty(300, dtype=torch.int32, device="cuda")
+    bad.infer_device(d_ev, d_lp, d_post, d_st, stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert np.all(d_st.cpu().numpy() == J.JT_CASE_INCOMPLETE)
+    assert np.all(np.isnan(d_lp.cpu().numpy()))
+    assert_parity32(*good.infer(ev), *_oracle(net, ev), where="after an expired wait")
