@@ -170,7 +170,7 @@ SERVING_PLANS = ["bn60", "bn110", "bn420", "bn1000"]
 
 
 def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, max_batch: int = 64,
-                arena_gb: float = 48.0):
+                arena_gb: float = 48.0, schedule=None):
     """The serving mix: resident plans of the four networks, one-case requests
     on a uniformly chosen plan with 5-30 % observed, Poisson arrivals at
     fractions of the measured saturated rate.  Returns p50/p99 latency
@@ -180,7 +180,11 @@ def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, 
     from synth.bn import sample_cases
     rng = np.random.default_rng(seed)
     nets = [configs.network(nm) for nm in SERVING_PLANS]
-    plans = [J.Plan(n, cases_per_thread=1) for n in nets]
+    # small batches: 32-case tiles; many plans share the GPU, so each pass
+    # runs layer by layer (a persistent dataflow pass would hold every SM
+    # until it ends and queue the other plans' short passes behind it)
+    sched = J.JT_SCHEDULE_LAYERS if schedule is None else schedule
+    plans = [J.Plan(n, cases_per_thread=1, schedule=sched) for n in nets]
     pool = [sample_cases(n, 2048, (0.05, 0.30), seed + i) for i, n in enumerate(nets)]
 
     def drive(srv, pids, n_req, rate):
@@ -215,6 +219,7 @@ def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, 
     sat = n_sat / drive(srv, pids, n_sat, None)
     srv.close()
     out = {"plans": SERVING_PLANS, "max_batch": max_batch, "arena_gb": arena_gb,
+           "schedule": "layers" if sched == J.JT_SCHEDULE_LAYERS else "dataflow",
            "saturated_cases_per_s": sat, "rates": []}
     for f in rates:
         rate = f * sat

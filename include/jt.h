@@ -87,7 +87,10 @@ enum {
  * one (Section 2's layer-by-layer order).  DATAFLOW: one launch per pass;
  * case tiles are independent, so a clique's work on a tile starts as soon
  * as its own producers on that tile are done, and the small layers near the
- * root of one tile overlap the large layers of others. */
+ * root of one tile overlap the large layers of others.  A dataflow pass
+ * holds every SM until it ends: when several plans share the GPU (a
+ * server), LAYERS lets their short passes interleave and gives lower
+ * latency. */
 enum { JT_SCHEDULE_DATAFLOW = 0, JT_SCHEDULE_LAYERS = 1 };
 
 typedef struct {
