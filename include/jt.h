@@ -10,10 +10,13 @@
  * table (Section 1), and every query passes messages along the tree with
  * the three table operations of Section 2 -- marginalisation, extension and
  * reduction (evidence) -- plus Hugin separator division.  Cliques are
- * grouped into tree layers (Section 2, BFS traversal); one GPU launch
- * processes a whole layer for a whole batch of evidence cases, which is the
- * GPU counterpart of the paper's per-layer flattening of all table entries
- * into one parallel task (Section 2, hybrid parallelism).
+ * grouped into tree layers (Section 2, BFS traversal) and every table entry
+ * of every clique is work for a whole batch of evidence cases at once, the
+ * GPU counterpart of the paper's flattening of a layer's table entries into
+ * one parallel task (Section 2, hybrid parallelism).  By default each pass
+ * (collect, distribute) is one GPU launch that takes the work in layer
+ * order and lets each case tile advance as soon as its own producers are
+ * done; JT_SCHEDULE_LAYERS runs one launch per layer instead.
  *
  * Conventions shared by every call:
  *   - Variables are numbered 0..n-1.  card[v] >= 2 is the number of states.
@@ -245,8 +248,9 @@ JT_API jt_status jt_infer_plain(jt_plan *plan, int32_t n_cases, const int32_t *e
 
 /*
  * Instrumented run of jt_infer_device (device buffers, same arguments) for
- * measurement: the layer launches are issued one by one (no graph) with a
- * CUDA event around each, on cuda_stream, and the call synchronises.
+ * measurement: the pass launches (one per pass in the dataflow schedule,
+ * one per layer in the layer schedule) are issued one by one (no graph)
+ * with a CUDA event around each, on cuda_stream, and the call synchronises.
  * out[0] total ms of the collect launches, out[1] total ms of the
  * distribute launches, out[2] ms of the evidence and finalize launches,
  * out[3] number of collect launches, out[4] number of distribute launches,
@@ -260,12 +264,12 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
  * Autotuner (no counterpart in the paper): compiles the network with each
  * candidate tile shape -- cases per thread in {4, 8} and work items per
  * tile and layer in {96, 192, 384} -- times the collect and the distribute
- * launches of n_cases cases separately on the current device (CUDA events
- * around every launch, best of three runs after a warm-up), picks per tile
+ * launches of n_cases cases separately on the current device (jt_profile,
+ * best of three runs after a warm-up) in base's schedule, picks per tile
  * width the best items value of each pass, and writes the fastest
- * combination to *best (base fields kept) and its layer-kernel time per
- * case in ns to *best_ns_per_case (may be NULL).  base may be NULL for the
- * defaults.  Allocates and frees its own device memory.
+ * combination to *best (base fields kept) and its pass time per case in ns
+ * to *best_ns_per_case (may be NULL).  base may be NULL for the defaults.
+ * Allocates and frees its own device memory.
  */
 JT_API jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
                              const int32_t *parents, const double *cpt, const jt_compile_opts *base,

@@ -124,8 +124,9 @@ void enqueue_distribute_layer(const jt_plan *pl, const DevArena &A, int L, cudaS
   launch_distribute(P.cpt_per_thread, pl->dp, A, lv.d_item_begin, lv.d_item_end - lv.d_item_begin, s);
 }
 
-// Enqueue the layer launches of one chunk: collect deepest layer first,
-// then distribute from the root down (Section 2's BFS layers).
+// Enqueue the two passes of one chunk in Section 2's BFS layer order
+// (collect from the deepest layer up, distribute from the root down): one
+// launch per layer, or one dataflow launch per pass.
 void enqueue_passes(const jt_plan *pl, const DevArena &A, cudaStream_t s) {
   const Plan &P = pl->P;
   const ArenaLayout L = arena_layout(P);
@@ -144,8 +145,6 @@ void enqueue_passes(const jt_plan *pl, const DevArena &A, cudaStream_t s) {
   launch_distribute_flow(P.cpt_per_thread, pl->dp, A, pl->flow_distribute_blocks, s);
 }
 
-static void enqueue_layers(const jt_plan *pl, const DevArena &A, cudaStream_t s) { enqueue_passes(pl, A, s); }
-
 static jt_status graph_for(jt_plan *pl, Arena &a, int tiles, cudaGraphExec_t *out) {
   auto it = a.graphs.find(tiles);
   if (it != a.graphs.end()) { *out = it->second; return JT_OK; }
@@ -153,7 +152,7 @@ static jt_status graph_for(jt_plan *pl, Arena &a, int tiles, cudaGraphExec_t *ou
   A.tiles = tiles;
   cudaGraph_t g = nullptr;
   JT_CUDA_TRY(cudaStreamBeginCapture(pl->capture_stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_layers(pl, A, pl->capture_stream);
+  enqueue_passes(pl, A, pl->capture_stream);
   cudaError_t e = cudaStreamEndCapture(pl->capture_stream, &g);
   if (e != cudaSuccess) {
     set_error(std::string("graph capture: ") + cudaGetErrorString(e));
@@ -188,7 +187,7 @@ jt_status run_chunk(jt_plan *pl, Arena &a, const int32_t *d_ev, int32_t nc, doub
     if (st != JT_OK) return st;
     JT_CUDA_TRY(cudaGraphLaunch(ex, s));
   } else {
-    enqueue_layers(pl, A, s);
+    enqueue_passes(pl, A, s);
   }
   launch_finalize(P.cpt_per_thread, pl->dp, A, nc, P.dcl[P.root].sep_row, d_lp, d_post, d_st, s);
   JT_CUDA_TRY(cudaGetLastError());

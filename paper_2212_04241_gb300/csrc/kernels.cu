@@ -1,15 +1,18 @@
 // Message kernels of the batched FP32 junction-tree path and of the plain
 // FP64 comparator path.
 //
-// Batched path.  One launch per tree layer and pass covers every clique of
-// that layer (Section 2: BFS layers, all table entries of a layer packed
-// into one parallel task) for every evidence case of the chunk: the grid is
-// (thread blocks of the layer's work list) x (case tiles).  Tables are
-// [tile][row][W] with W = 32 * CPT consecutive evidence cases per row; a
-// warp owns a contiguous range of rows of one table and moves one whole row
-// (W * 4 bytes, fully coalesced) per access, so every index computation is
-// shared by the W cases of a row.  Row indices are computed 32 rows at a
-// time, one row per lane, and broadcast; rows are loaded four at a time.
+// Batched path.  The unit of work is one warp's item (a row range of one
+// clique's table, or of one distribute task) on one case tile.  Section 2
+// packs all table entries of a BFS layer into one parallel task; here either
+// one launch per layer and pass covers every item of the layer for every
+// case tile (layer schedule: grid = item blocks x tiles), or one persistent
+// launch per pass takes (item, tile) units in layer order and starts each
+// as soon as its producers on the same tile are done (dataflow schedule).
+// Tables are [tile][row][W] with W = 32 * CPT consecutive evidence cases per
+// row; a warp moves one whole row (W * 4 bytes, fully coalesced) per access,
+// so every index computation is shared by the W cases of a row.  Row indices
+// are computed 32 rows at a time, one row per lane, and broadcast; rows are
+// loaded four at a time (two at 8 cases per thread).
 //
 //   collect (Section 2: reduction + extension + marginalisation, fused):
 //     psi_C[e] = base_C[e] * [evidence entered in C] *
