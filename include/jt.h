@@ -263,7 +263,7 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
 /*
  * Autotuner (no counterpart in the paper): compiles the network with each
  * candidate tile shape -- cases per thread in {4, 8} and work items per
- * tile and layer in {96, 192, 384} -- times the collect and the distribute
+ * tile and layer in {96, 192, 384, 768, 1536} -- times the collect and the distribute
  * launches of n_cases cases separately on the current device (jt_profile,
  * best of three runs after a warm-up) in base's schedule, picks per tile
  * width the best items value of each pass, and writes the fastest

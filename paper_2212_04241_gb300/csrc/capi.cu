@@ -801,7 +801,7 @@ extern "C" jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int3
   if (base) b = *base; else jt_default_opts(&b);
   b.host_only = 0;
   const int cpts[] = {4, 8};
-  const int items[] = {96, 192, 384};
+  const int items[] = {96, 192, 384, 768, 1536};
   int64_t sum_card = 0;
   for (int v = 0; v < n_vars; ++v) sum_card += card[v];
   int32_t *d_ev = nullptr;
@@ -826,7 +826,7 @@ extern "C" jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int3
     const int cw = (base && base->cases_per_thread != 0) ? base->cases_per_thread : cpts[ci];
     double best_c = -1, best_d = -1;
     int item_c = 192, item_d = 192;
-    for (int ii = 0; result == JT_OK && ii < 3; ++ii) {
+    for (int ii = 0; result == JT_OK && ii < (int)(sizeof(items) / sizeof(items[0])); ++ii) {
       jt_compile_opts o = b;
       o.cases_per_thread = cw;
       o.items_per_tile = items[ii];

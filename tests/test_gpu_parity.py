@@ -255,8 +255,8 @@ def test_autotuned_plan_parity():
     net = configs.network("bn60")
     ev = configs.evidence("bn60", net, n_cases=512)
     opts, ns = J.autotune(net, 512)
-    assert opts["cases_per_thread"] in (4, 8) and opts["items_per_tile"] in (96, 192, 384)
-    assert opts["items_per_tile_distribute"] in (96, 192, 384)
+    assert opts["cases_per_thread"] in (4, 8) and opts["items_per_tile"] in (96, 192, 384, 768, 1536)
+    assert opts["items_per_tile_distribute"] in (96, 192, 384, 768, 1536)
     assert ns > 0
     p = J.Plan(net, **opts)
     assert_parity32(*p.infer(ev), *_oracle(net, ev), where=f"autotuned {opts}")
