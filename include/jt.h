@@ -129,7 +129,18 @@ typedef struct {
                                  the collect work of clique k-1 wait for one
                                  producer more than exists, so its waits
                                  expire (exercises JT_ETIMEOUT) */
-  int32_t reserved[2];
+  int32_t n_observed_set;     /* specialise the plan to an observed set: */
+  const int32_t *observed_set;/* n_observed_set distinct variables that EVERY
+                                 case run on the plan observes (their states
+                                 vary from case to case).  Their dimensions
+                                 are sliced out of every clique and separator
+                                 table (each case reads its own slice of the
+                                 base tables), which shrinks the tables by
+                                 the product of those cardinalities; a case
+                                 leaving one of them unobserved gets
+                                 JT_CASE_BAD_EVIDENCE.  NULL / 0 = none.
+                                 Read during jt_compile only.  Sliced plans
+                                 support every call except jt_infer_plain. */
 } jt_compile_opts;
 
 typedef struct {
@@ -149,6 +160,7 @@ typedef struct {
   int64_t distribute_items;     /* thread blocks per tile, all distribute layers */
   double algorithmic_bytes_per_case; /* 8*sum|C| + 16*sum|S| + 4n + 8*sum(card) + 8 */
   int32_t kernels_per_chunk;    /* kernel launches of one batch chunk */
+  int32_t sliced_vars;          /* size of the observed set sliced out (0: none) */
   int32_t separator_evidence_vars; /* variables whose evidence indicator is
                                  applied to an upward message (a separator
                                  smaller than every clique holding them)

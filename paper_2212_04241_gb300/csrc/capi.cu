@@ -268,6 +268,7 @@ static jt_status upload_plan(jt_plan *pl) {
   const size_t o_cfp = put(blob, P.c_flow_pref), o_cfb = put(blob, P.c_flow_begin);
   const size_t o_dfp = put(blob, P.d_flow_pref), o_dfb = put(blob, P.d_flow_begin);
   const size_t o_cn = put(blob, P.c_need), o_cno = put(blob, P.c_notify), o_dn = put(blob, P.d_need);
+  const size_t o_sv = put(blob, P.slice_var);
   JT_CUDA_TRY(cudaMalloc(&pl->d_static, blob.size()));
   pl->static_bytes = blob.size();
   JT_CUDA_TRY(cudaMemcpy(pl->d_static, blob.data(), blob.size(), cudaMemcpyHostToDevice));
@@ -297,6 +298,7 @@ static jt_status upload_plan(jt_plan *pl) {
   D.c_need = reinterpret_cast<const uint32_t *>(b + o_cn);
   D.c_notify = reinterpret_cast<const int32_t *>(b + o_cno);
   D.d_need = reinterpret_cast<const uint32_t *>(b + o_dn);
+  D.slice_var = P.n_sliced > 0 ? reinterpret_cast<const int32_t *>(b + o_sv) : nullptr;
   D.n_flow_layers = P.height + 1;
   D.wait_limit_ns = 1000ull * (uint64_t)(P.opts.wait_limit_us > 0 ? P.opts.wait_limit_us : 2000000);
   D.n_pgroups = (int32_t)P.pgroup_ptr.size() - 1;
@@ -425,6 +427,7 @@ extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
     k += 2;  // one dataflow launch per pass
   }
   o->kernels_per_chunk = k;
+  o->sliced_vars = P.n_sliced;
   o->separator_evidence_vars = 0;
   for (const HostClique &C : P.cl) o->separator_evidence_vars += (int32_t)C.ev_sep.size();
   return JT_OK;
@@ -652,6 +655,7 @@ extern "C" jt_status jt_infer_plain(jt_plan *pl, int32_t n_cases, const int32_t 
                                     double *post, int32_t *cst, void *stream) {
   if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
   if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
+  if (pl->P.n_sliced > 0) { set_error("the plain path runs unspecialised plans only"); return JT_EINVAL; }
   if (n_cases == 0) return JT_OK;
   if (!ev || !lp || !post || !cst) { set_error("null buffer"); return JT_EINVAL; }
   std::lock_guard<std::mutex> lk(pl->mu);

@@ -277,6 +277,23 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   P.post_off.assign(n, 0);
   P.sum_card = 0;
   for (int v = 0; v < n; ++v) { P.post_off[v] = P.sum_card; P.sum_card += card[v]; }
+  // observed set of a specialised plan
+  P.slice_var.assign(n, 0);
+  P.n_sliced = 0;
+  if (opts.n_observed_set < 0 || (opts.n_observed_set > 0 && opts.observed_set == nullptr)) {
+    err = "bad observed set";
+    return JT_EINVAL;
+  }
+  for (int i = 0; i < opts.n_observed_set; ++i) {
+    const int v = opts.observed_set[i];
+    if (v < 0 || v >= n || P.slice_var[v]) {
+      err = "observed set: variable out of range or listed twice";
+      return JT_EINVAL;
+    }
+    P.slice_var[v] = 1;
+    ++P.n_sliced;
+  }
+  auto sliced = [&](int v) { return P.slice_var[v] != 0; };
 
   // moral graph
   const int W = (n + 63) / 64;
@@ -371,6 +388,38 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     if (C.parent >= 0) P.cl[C.parent].children.push_back(c);
   }
   for (auto &C : P.cl) std::sort(C.children.begin(), C.children.end());
+  // Full layout (base tables) and, in a specialised plan, the sliced layout
+  // of every other table: the observed set's variables left out, the order
+  // kept (so each child's upward separator stays a prefix in its parent's
+  // order).
+  for (auto &C : P.cl) {
+    C.fvars = C.vars;
+    C.fstride = C.stride;
+    C.fsize = C.size;
+    if (P.n_sliced == 0) continue;
+    std::vector<int> v2;
+    int up2 = 0;
+    for (int i = 0; i < (int)C.vars.size(); ++i) {
+      if (sliced(C.vars[i])) continue;
+      v2.push_back(C.vars[i]);
+      if (i < C.n_up) ++up2;
+    }
+    C.vars = v2;
+    C.n_up = up2;
+    const int k = (int)C.vars.size();
+    C.card.assign(k, 0);
+    C.stride.assign(k, 0);
+    int64_t s2 = 1;
+    for (int i = k - 1; i >= 0; --i) {
+      C.card[i] = card[C.vars[i]];
+      C.stride[i] = s2;
+      s2 *= C.card[i];
+    }
+    C.size = s2;
+    C.nsep = 1;
+    for (int i = 0; i < C.n_up; ++i) C.nsep *= C.card[i];
+    C.R = C.size / C.nsep;
+  }
 
   // CPT assignment (smallest clique containing the family, lowest id on
   // ties); posterior owner (smallest clique containing the variable)
@@ -391,6 +440,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   // table holding it -- a separator (its calibrated marginal is phi* x rho)
   // when one is no larger than the smallest clique, else that clique.
   for (int v = 0; v < n; ++v) {
+    if (sliced(v)) continue;  // always observed: a point mass, no table needed
     int best_sep = -1;
     double best_sep_size = 0;
     for (int c = 0; c < m; ++c) {
@@ -401,7 +451,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       for (int i = 0; i < C.n_up; ++i) sz *= C.card[i];
       if (best_sep < 0 || sz < best_sep_size) { best_sep = c; best_sep_size = sz; }
     }
-    if (best_sep >= 0 && best_sep_size <= csize[P.post_src[v]])
+    if (best_sep >= 0 && best_sep_size <= (double)P.cl[P.post_src[v]].size)
       P.cl[best_sep].owned_sep.push_back(v);
     else
       P.cl[P.post_src[v]].owned.push_back(v);
@@ -417,6 +467,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   // entry is written) or a clique (one indicator per clique entry), ties to
   // the separator and then to the lowest clique id.
   for (int v = 0; v < n; ++v) {
+    if (sliced(v)) continue;  // sliced out: each case reads its own slice
     int best = -1;
     bool best_sep = false;
     int64_t best_cost = 0;
@@ -439,39 +490,47 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     (best_sep ? P.cl[best].ev_sep : P.cl[best].ev_clique).push_back(v);
   }
 
-  P.sum_cl = P.max_cl = P.sum_sep = 0;
+  P.sum_cl = P.max_cl = P.sum_sep = P.sum_base = 0;
   for (int c = 0; c < m; ++c) {
     P.sum_cl += P.cl[c].size;
+    P.sum_base += P.cl[c].fsize;
     P.max_cl = std::max(P.max_cl, P.cl[c].size);
     if (c != root) P.sum_sep += P.cl[c].nsep;
   }
 
-  // base tables: product of the assigned CPTs, in each clique's layout
-  P.base64.assign(P.sum_cl, 1.0);
-  P.base32.assign(P.sum_cl, 1.0f);
+  // base tables: product of the assigned CPTs, in each clique's full layout
+  P.base64.assign(P.sum_base, 1.0);
+  P.base32.assign(P.sum_base, 1.0f);
   P.p_base_off.assign(m, 0);
   std::vector<int64_t> psi_row(m, 0);
   {
-    int64_t off = 0;
-    for (int c = 0; c < m; ++c) { P.p_base_off[c] = off; psi_row[c] = off; off += P.cl[c].size; }
+    int64_t off = 0, prow = 0;
+    for (int c = 0; c < m; ++c) {
+      P.p_base_off[c] = off;
+      off += P.cl[c].fsize;
+      psi_row[c] = prow;
+      prow += P.cl[c].size;
+    }
   }
   for (int v = 0; v < n; ++v) {
     const HostClique &C = P.cl[P.assign[v]];
     // weight of each clique variable inside v's CPT (parents listed order, child fastest)
-    std::vector<int64_t> w(C.vars.size(), 0);
+    std::vector<int64_t> w(C.fvars.size(), 0);
     int64_t s = 1;
-    auto pos_of = [&](int x) { return (int)(std::find(C.vars.begin(), C.vars.end(), x) - C.vars.begin()); };
+    auto pos_of = [&](int x) { return (int)(std::find(C.fvars.begin(), C.fvars.end(), x) - C.fvars.begin()); };
     w[pos_of(v)] = s;
     s *= card[v];
     for (int k = pptr[v + 1] - 1; k >= pptr[v]; --k) {
       w[pos_of(par[k])] = s;
       s *= card[par[k]];
     }
+    std::vector<int> fcard;
+    for (int x : C.fvars) fcard.push_back(card[x]);
     std::vector<int32_t> idx;
-    linear_table(C.card, w, idx);
+    linear_table(fcard, w, idx);
     double *b = P.base64.data() + P.p_base_off[P.assign[v]];
     const double *t = P.cpt.data() + P.cpt_off[v];
-    for (int64_t e = 0; e < C.size; ++e) b[e] *= t[idx[e]];
+    for (int64_t e = 0; e < C.fsize; ++e) b[e] *= t[idx[e]];
   }
   // FP32 copy, each clique scaled by a power of two so that its maximum is
   // in [1, 2); the exponents are a per-plan constant added to log P(e)
@@ -479,11 +538,11 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   for (int c = 0; c < m; ++c) {
     const double *b = P.base64.data() + P.p_base_off[c];
     double mx = 0;
-    for (int64_t e = 0; e < P.cl[c].size; ++e) mx = std::max(mx, b[e]);
+    for (int64_t e = 0; e < P.cl[c].fsize; ++e) mx = std::max(mx, b[e]);
     int ex = 0;
     if (mx > 0) { std::frexp(mx, &ex); ex -= 1; }
     base_exp[c] = ex;
-    for (int64_t e = 0; e < P.cl[c].size; ++e)
+    for (int64_t e = 0; e < P.cl[c].fsize; ++e)
       P.base32[P.p_base_off[c] + e] = (float)std::ldexp(b[e], -ex);
   }
 
@@ -579,6 +638,29 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       P.dmap.push_back(mp);
     }
     D.sev_end = (int32_t)P.dmap.size();
+    // sliced plan: the clique's observed-set variables (stride in the full
+    // base table) and the base entry of each table entry
+    D.slice_begin = D.sev_end;
+    D.bmap_A = D.bmap_B = zero_off;
+    if (P.n_sliced > 0) {
+      for (size_t i = 0; i < C.fvars.size(); ++i) {
+        if (!sliced(C.fvars[i])) continue;
+        DMap mp{};
+        mp.kind = MAP_SLICE;
+        mp.src = C.fvars[i];
+        mp.A_off = C.fstride[i];
+        P.dmap.push_back(mp);
+      }
+      auto fstride_of = [&](int v) {
+        return C.fstride[std::find(C.fvars.begin(), C.fvars.end(), v) - C.fvars.begin()];
+      };
+      std::vector<int64_t> wa(C.n_up, 0), wb(C.vars.size() - C.n_up, 0);
+      for (int i = 0; i < (int)C.vars.size(); ++i)
+        (i < C.n_up ? wa[i] : wb[i - C.n_up]) = fstride_of(C.vars[i]);
+      D.bmap_A = table_or_zero(up_card, wa);
+      D.bmap_B = table_or_zero(res_card, wb);
+    }
+    D.slice_end = (int32_t)P.dmap.size();
   }
   P.cpt_per_thread = opts.cases_per_thread > 0 ? opts.cases_per_thread : 4;
   if (P.cpt_per_thread != 1 && P.cpt_per_thread != 2 && P.cpt_per_thread != 4 && P.cpt_per_thread != 8) {
@@ -794,10 +876,16 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     std::vector<int> comp_root(m, -1);
     for (int c : P.bfs) comp_root[c] = (c == root || P.cl[c].n_up == 0) ? c : comp_root[P.cl[c].parent];
     std::vector<std::vector<int32_t>> members_of(m);
-    std::vector<char> seen(n, 0);
-    for (int c : P.bfs)
-      for (int v : P.cl[c].vars)
+    // every variable of the component's tables; an observed-set variable
+    // (sliced out of the tables, but read through the base tables) is listed
+    // in every component whose cliques hold it
+    std::vector<std::vector<char>> seen_in(m);
+    for (int c : P.bfs) {
+      std::vector<char> &seen = seen_in[comp_root[c]];
+      if (seen.empty()) seen.assign(n, 0);
+      for (int v : P.cl[c].fvars)
         if (!seen[v]) { seen[v] = 1; members_of[comp_root[c]].push_back(v); }
+    }
     P.comp_ptr.assign(m + 1, 0);
     P.comp_vars.clear();
     for (int c = 0; c < m; ++c) {
@@ -828,9 +916,11 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
 
   // ---------------------------------------------------------------------
   // plain FP64 path maps: (var, card, src stride, dst stride) quadruples
+  // (the comparator runs unspecialised plans only)
   // ---------------------------------------------------------------------
   P.pmap.clear();
   P.ppool.clear();
+  if (P.n_sliced > 0) return JT_OK;
   auto plain_map = [&](const HostClique &X, const std::vector<int> &dst_vars) -> int {
     // dst is row-major over dst_vars (last fastest)
     DPlainMap pm{};

@@ -32,7 +32,10 @@ struct DClique {
   int32_t comp_base_exp;  // component roots: sum of the component's base-table exponents
   int32_t sev_begin;  // evidence applied to its upward message as it is
   int32_t sev_end;    //   written: MAP_SEP_EVIDENCE maps [sev_begin, sev_end)
-  int32_t pad;
+  int32_t slice_begin;  // sliced plan: the clique's variables of the observed
+  int32_t slice_end;    //   set, MAP_SLICE maps [slice_begin, slice_end)
+  int64_t bmap_A;     // sliced plan: base-table entry of table entry s*R+u
+  int64_t bmap_B;     //   = A[s] + B[u] (int32 pool offsets); unused otherwise
 };
 
 // A linear index map over a clique's entries: idx(s*R + u) = A[s] + B[u].
@@ -42,7 +45,9 @@ struct DClique {
 //   kind MAP_SEP_EVIDENCE: the same over the entries s of the clique's
 //     upward message only (A[s] is the digit, B unused), applied to the
 //     message entry when it is written
-enum { MAP_CHILD = 0, MAP_EVIDENCE = 1, MAP_SEP_EVIDENCE = 2 };
+//   kind MAP_SLICE (sliced plan): variable `src` of the observed set in the
+//     clique; A_off is its stride in the full base table
+enum { MAP_CHILD = 0, MAP_EVIDENCE = 1, MAP_SEP_EVIDENCE = 2, MAP_SLICE = 3 };
 struct DMap {
   int64_t A_off;      // int32 pool offset, nsep entries
   int64_t B_off;      // int32 pool offset, R entries
@@ -100,10 +105,17 @@ struct DPlainMap {
 // ---------------------------------------------------------------------------
 
 struct HostClique {
+  // Layout of the clique's tables (psi, messages, maps).  In a plan
+  // specialised to an observed set O (every case observes the variables of
+  // O), the tables leave O's variables out ("sliced"); the base table keeps
+  // the full layout (fvars...) and each case reads the slice of its states.
   std::vector<int> vars;        // layout order: upward separator first
   std::vector<int> card;
   std::vector<int64_t> stride;  // stride of vars[i] in this table (last fastest)
   int64_t size = 1;
+  std::vector<int> fvars;       // full layout of the base table (= vars when nothing is sliced)
+  std::vector<int64_t> fstride;
+  int64_t fsize = 1;
   int n_up = 0;                 // number of upward-separator variables
   int64_t nsep = 1, R = 1;
   int parent = -1, depth = 0;
@@ -140,6 +152,9 @@ struct Plan {
   std::vector<int> assign;        // CPT v -> clique
   std::vector<int> post_src;      // variable -> smallest clique containing it
   int64_t sum_cl = 0, max_cl = 0, sum_sep = 0;
+  int64_t sum_base = 0;           // entries of the base tables (full layouts)
+  std::vector<int32_t> slice_var; // sliced plan: 1 for the variables of the observed set
+  int n_sliced = 0;
 
   // device-side description (host copies)
   std::vector<DClique> dcl;

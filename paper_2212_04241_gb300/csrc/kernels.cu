@@ -224,13 +224,17 @@ __global__ void k_evidence(const int32_t *__restrict__ ev_in, int32_t n_cases, D
     const int64_t c = c0 + i;
     const int v = v0 + threadIdx.x;
     int val = -1;
+    // a sliced plan's observed-set variables index the base tables: always a
+    // valid state (0 stands in where a case breaks the contract or pads the tile)
+    const bool in_set = P.slice_var != nullptr && v < P.n_vars && P.slice_var[v] != 0;
     if (v < P.n_vars && c < n_cases) {
       val = ev_in[c * P.n_vars + v];
-      if (val < -1 || val >= P.card[v]) {
+      if (val < -1 || val >= P.card[v] || (in_set && val < 0)) {
         A.bad[c] = 1;
         val = -1;
       }
     }
+    if (in_set && val < 0) val = 0;
     t[i][threadIdx.x] = val;
   }
   __syncthreads();
@@ -355,6 +359,21 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
   __syncwarp();
   const int32_t R = (int32_t)C.R;
   const float *__restrict__ base = P.base32 + C.base_off;
+  // sliced plan: each case reads the base-table slice of its observed-set
+  // states (offset in the full base table), entry e of the sliced table
+  // being base entry bA[s] + bB[u]
+  const bool sliced = C.slice_end > C.slice_begin;
+  int32_t boff[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) boff[k] = 0;
+  for (int i = C.slice_begin; i < C.slice_end; ++i) {
+    const DMap mp = P.maps[i];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+      boff[k] += A.ev[((int64_t)tile * P.n_vars + mp.src) * W + col_of<CPT>(lane, k)] * (int32_t)mp.A_off;
+  }
+  const int32_t *__restrict__ bA = P.ipool + C.bmap_A;
+  const int32_t *__restrict__ bB = P.ipool + C.bmap_B;
   float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
   float *phi_out = A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
 
@@ -378,14 +397,24 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
     // lane j: indices of row b0 + j
     const int64_t ej = e_first + b0 + min(lane, nb - 1);
     const int32_t sj = (int32_t)ej / R, uj = (int32_t)ej - sj * R;  // |C| < 2^31
-    const float bj = __ldg(base + ej);
+    const int32_t fj = sliced ? __ldg(bA + sj) + __ldg(bB + uj) : 0;  // base entry (sliced plan)
+    const float bj = sliced ? 0.f : __ldg(base + ej);
     for (int i = 0; i < nm; ++i) idx[i * 32 + lane] = __ldg(P.ipool + mA[i] + sj) + __ldg(P.ipool + mB[i] + uj);
     const unsigned last = __ballot_sync(kFull, !it.split && uj == R - 1 && lane < nb);
     __syncwarp();
     for (int r = 0; r < nb; r += G) {
       Vec<CPT> v[G];
+      if (!sliced) {
 #pragma unroll
-      for (int g = 0; g < G; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
+        for (int g = 0; g < G; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int32_t f = __shfl_sync(kFull, fj, min(r + g, nb - 1));
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) v[g].x[k] = __ldg(base + f + boff[k]);
+        }
+      }
       // child maps two at a time: both rows are requested before either is used
       for (int i = 0; i < nchild; i += 2) {
         const bool two = i + 1 < nchild;

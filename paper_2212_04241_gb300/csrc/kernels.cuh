@@ -37,6 +37,7 @@ struct DevPlan {
   const uint32_t *c_need;       // [n_cliques] collect items of the children that send a message
   const int32_t *c_notify;      // [n_cliques] parent that receives the clique's message, or -1
   const uint32_t *d_need;       // [n_cliques] items of the parent's task that writes the clique's ratio
+  const int32_t *slice_var;     // sliced plan: [n] 1 for the observed set; nullptr otherwise
   int32_t n_flow_layers;
   uint64_t wait_limit_ns;       // bound of a dataflow wait
   int32_t n_comp;

@@ -34,7 +34,7 @@ class CompileOpts(ctypes.Structure):
                 ("use_graphs", ctypes.c_int32), ("items_per_tile", ctypes.c_int32),
                 ("items_per_tile_distribute", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("wait_limit_us", ctypes.c_int32), ("stall_clique", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("n_observed_set", ctypes.c_int32), ("observed_set", ctypes.c_void_p)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -46,7 +46,8 @@ class PlanInfo(ctypes.Structure):
                 ("arena_bytes", ctypes.c_int64), ("static_device_bytes", ctypes.c_int64),
                 ("collect_items", ctypes.c_int64), ("distribute_items", ctypes.c_int64),
                 ("algorithmic_bytes_per_case", ctypes.c_double),
-                ("kernels_per_chunk", ctypes.c_int32), ("separator_evidence_vars", ctypes.c_int32)]
+                ("kernels_per_chunk", ctypes.c_int32), ("sliced_vars", ctypes.c_int32),
+                ("separator_evidence_vars", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -110,10 +111,18 @@ def _ptr(a):
 
 
 def default_opts(**kw) -> CompileOpts:
+    """jt_compile_opts with the defaults, then the given fields.  observed_set
+    takes a sequence of variable ids (kept alive with the returned struct)."""
     o = CompileOpts()
     lib.jt_default_opts(ctypes.byref(o))
+    obs = kw.pop("observed_set", None)
     for k, v in kw.items():
         setattr(o, k, v)
+    if obs is not None and len(obs) > 0:
+        arr = np.ascontiguousarray(obs, dtype=np.int32)
+        o._observed_keepalive = arr
+        o.n_observed_set = int(arr.size)
+        o.observed_set = arr.ctypes.data
     return o
 
 
@@ -139,6 +148,8 @@ def autotune(net, n_cases: int, **opts):
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
                                            "items_per_tile_distribute", "use_graphs", "arena_bytes",
                                            "max_clique_entries", "schedule")}
+    if opts.get("observed_set") is not None:
+        out["observed_set"] = list(opts["observed_set"])
     return out, ns.value
 
 

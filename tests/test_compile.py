@@ -159,3 +159,29 @@ def test_schedule_option():
     with pytest.raises(J.JTError) as e:
         J.Plan(net, host_only=1, stall_clique=layers["n_cliques"] + 1)
     assert e.value.status == J.JT_EINVAL
+
+
+def test_observed_set_option():
+    """A plan specialised to an observed set leaves those variables out of
+    every clique and separator table: the tables shrink by the product of
+    their cardinalities over each clique holding them; the base tables keep
+    the full layout."""
+    net = configs.network("bn60")
+    full = _plan(net).info()
+    obs = [2, 15, 18, 29, 35, 46]
+    p = _plan(net, observed_set=obs)
+    info = p.info()
+    assert info["sliced_vars"] == len(obs)
+    assert info["n_cliques"] == full["n_cliques"]
+    assert info["sum_clique_entries"] < full["sum_clique_entries"]
+    size = lambda vs: int(np.prod([net.card[v] for v in vs])) if vs else 1
+    total = 0
+    for c in range(info["n_cliques"]):
+        vars_, _, _ = p.clique(c)
+        assert not set(vars_) & set(obs)
+        total += size(vars_)
+    assert total == info["sum_clique_entries"]
+    for bad in ([3, 3], [60], [-1]):
+        with pytest.raises(J.JTError) as e:
+            _plan(net, observed_set=bad)
+        assert e.value.status == J.JT_EINVAL
