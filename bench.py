@@ -283,6 +283,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix latency measurement")
     ap.add_argument("--no-autotune", action="store_true", help="default plan options instead of jt_autotune")
+    ap.add_argument("--observed-set", type=int, default=0,
+                    help="K > 0: every case observes the same K variables (seeded choice, states from an "
+                    "ancestral sample) and the plan is specialised to that set")
     ap.add_argument("--plan", default="", help="fixed plan options as JSON (e.g. '{\"items_per_tile\": 96}'), "
                     "instead of jt_autotune")
     ap.add_argument("--serving-only", action="store_true", help="only the serving-mix measurement")
@@ -299,6 +302,15 @@ def main():
     n_cases = args.cases or DEFAULT_CASES[name]
     # every rank gets its own independent batch (weak scaling)
     ev = configs.evidence(name, net, n_cases=n_cases, seed=rank_evidence_seed(name, rank))
+    observed_set = None
+    if args.observed_set > 0:
+        # a fixed observed set shared by every case (its states vary per case)
+        from synth.bn import sample_cases
+        rng = np.random.default_rng(1234)
+        observed_set = sorted(int(v) for v in rng.choice(net.n, size=args.observed_set, replace=False))
+        x = sample_cases(net, n_cases, 1.0, seed=rank_evidence_seed(name, rank))
+        ev = np.full_like(x, -1, dtype=np.int32)
+        ev[:, observed_set] = x[:, observed_set]
 
     if args.impl == "reference":
         return run_reference(args, name, net, ev, rank, world)
@@ -315,10 +327,11 @@ def main():
 
     import paper_2212_04241_gb300.jt as J
     # the library's autotuner picks the tile shape for this network and batch
+    spec = {"observed_set": observed_set} if observed_set else {}
     if args.plan:
-        tuned = json.loads(args.plan)
+        tuned = dict(json.loads(args.plan), **spec)
     else:
-        tuned, _ = J.autotune(net, n_cases) if not args.no_autotune else ({}, None)
+        tuned, _ = J.autotune(net, n_cases, **spec) if not args.no_autotune else (dict(spec), None)
     plan = J.Plan(net, **tuned)
     stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
@@ -454,10 +467,11 @@ def main():
         "value": value, "unit": "cases/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[name], "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
+        "config": {"workload": WORKLOADS[name] + (f"_observedset{args.observed_set}" if observed_set else ""),
+                   "observed_set": observed_set, "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
                    "chunk_cases": info["chunk_cases"], "levels": info["n_levels"],
-                   "autotuned": ({k: tuned[k] for k in ("cases_per_thread", "items_per_tile", "items_per_tile_distribute")}
-                                 if tuned and not args.plan else None),
+                   "autotuned": ({k: tuned.get(k) for k in ("cases_per_thread", "items_per_tile", "items_per_tile_distribute")}
+                                 if tuned and not args.plan and not args.no_autotune else None),
                    "plan_options": tuned if args.plan else None,
                    "schedule": "dataflow" if dataflow else "layers",
                    "sum_clique_entries": info["sum_clique_entries"],
