@@ -293,6 +293,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     P.slice_var[v] = 1;
     ++P.n_sliced;
   }
+  P.opts.observed_set = nullptr;  // the caller's array is read during compilation only
   auto sliced = [&](int v) { return P.slice_var[v] != 0; };
 
   // moral graph
