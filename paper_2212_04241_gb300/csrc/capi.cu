@@ -317,7 +317,7 @@ static jt_status upload_plan(jt_plan *pl) {
     set_error("a clique has too many child messages and evidence variables for one warp's shared memory");
     return JT_ETOOBIG;
   }
-  JT_CUDA_TRY(configure_collect_smem(P.cpt_per_thread, smem));
+  JT_CUDA_TRY(configure_collect_smem(P.cpt_per_thread, P.n_sliced > 0, smem));
   if (logpe_smem_bytes((int)P.comp_roots.size()) > 220 * 1024) {
     set_error("the network splits into too many independent component trees for the log P(e) kernel");
     return JT_ETOOBIG;
@@ -325,8 +325,8 @@ static jt_status upload_plan(jt_plan *pl) {
   JT_CUDA_TRY(configure_logpe_smem((int)P.comp_roots.size()));
   int sms = 0;
   JT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
-  pl->flow_collect_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, true, max_maps);
-  pl->flow_distribute_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, false, 0);
+  pl->flow_collect_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, true, P.n_sliced > 0, max_maps);
+  pl->flow_distribute_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, false, false, 0);
   return JT_OK;
 }
 

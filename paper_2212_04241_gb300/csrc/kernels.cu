@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -318,8 +319,9 @@ __host__ __device__ inline size_t collect_warp_smem(int cpt, int nm) {
 // One collect work item (a warp's rows of one clique, one case tile).  MSG
 // is the load path of the children's messages: the read-only path when an
 // earlier kernel wrote them, coherent loads when warps of the same kernel
-// did (dataflow schedule).
-template <int CPT, LoadMode MSG>
+// did (dataflow schedule).  SLICED instantiates the base-table gather of
+// plans specialised to an observed set; other plans compile without it.
+template <int CPT, LoadMode MSG, bool SLICED>
 __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
                                              unsigned char *ws, int max_maps, int lane) {
   constexpr int W = 32 * CPT;
@@ -362,11 +364,11 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
   // sliced plan: each case reads the base-table slice of its observed-set
   // states (offset in the full base table), entry e of the sliced table
   // being base entry bA[s] + bB[u]
-  const bool sliced = C.slice_end > C.slice_begin;
+  const bool sliced = SLICED && C.slice_end > C.slice_begin;
   int32_t boff[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) boff[k] = 0;
-  for (int i = C.slice_begin; i < C.slice_end; ++i) {
+  for (int i = C.slice_begin; SLICED && i < C.slice_end; ++i) {
     const DMap mp = P.maps[i];
 #pragma unroll
     for (int k = 0; k < CPT; ++k)
@@ -491,15 +493,15 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
     if (mx.x[k] > 0.f) atomicMax(mb + col_of<CPT>(lane, k), __float_as_uint(mx.x[k]));
 }
 
-template <int CPT>
+template <int CPT, bool SLICED>
 __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPlan P, DevArena A, int64_t item_begin,
                                                           int64_t n_items, int max_maps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (iw >= n_items) return;
-  collect_item<CPT, LD_NC>(P, A, P.citems[item_begin + iw], blockIdx.y,
-                           smem_raw + (size_t)warp * collect_warp_smem(CPT, max_maps), max_maps, lane);
+  collect_item<CPT, LD_NC, SLICED>(P, A, P.citems[item_begin + iw], blockIdx.y,
+                                   smem_raw + (size_t)warp * collect_warp_smem(CPT, max_maps), max_maps, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -685,7 +687,7 @@ __device__ __forceinline__ bool next_unit(unsigned long long *queue, const int64
   return true;
 }
 
-template <int CPT>
+template <int CPT, bool SLICED>
 __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect_flow(DevPlan P, DevArena A, int max_maps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -697,7 +699,7 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect_flow(
     uint32_t *ready = A.ready + (int64_t)tile * 2 * P.n_cliques;
     const uint32_t need = P.c_need[it.task];
     if (need == 0u || wait_ready(ready + it.task, need, A.errflag, P.wait_limit_ns, lane))
-      collect_item<CPT, LD_PLAIN>(P, A, it, tile, ws, max_maps, lane);
+      collect_item<CPT, LD_PLAIN, SLICED>(P, A, it, tile, ws, max_maps, lane);
     const int parent = P.c_notify[it.task];
     signal_done(parent >= 0 ? ready + parent : nullptr, lane);
   }
@@ -927,35 +929,44 @@ static int collect_warps(int cpt, int max_maps) {
   return (int)std::min<size_t>(kWarps, std::max<size_t>(1, kCollectSmemLimit / std::max<size_t>(per_warp, 1)));
 }
 
-template <int CPT>
-static void collect_t(const DevPlan &P, const DevArena &A, int64_t b, int64_t n, int max_maps, cudaStream_t s) {
-  const int nw = collect_warps(CPT, max_maps);
-  const size_t smem = (size_t)nw * collect_warp_smem(CPT, max_maps);
-  dim3 grid((unsigned)((n + nw - 1) / nw), (unsigned)A.tiles);
-  k_collect<CPT><<<grid, 32 * nw, smem, s>>>(P, A, b, n, max_maps);
+// Calls f(CPT, SLICED) with both as compile-time constants: the collect
+// kernels are instantiated per cases-per-thread and per plan kind.
+template <class F>
+static auto with_collect(int cpt, bool sliced, F &&f) {
+  using std::integral_constant;
+  using yes = std::true_type;
+  using no = std::false_type;
+  if (cpt == 8) return sliced ? f(integral_constant<int, 8>{}, yes{}) : f(integral_constant<int, 8>{}, no{});
+  if (cpt == 4) return sliced ? f(integral_constant<int, 4>{}, yes{}) : f(integral_constant<int, 4>{}, no{});
+  if (cpt == 2) return sliced ? f(integral_constant<int, 2>{}, yes{}) : f(integral_constant<int, 2>{}, no{});
+  return sliced ? f(integral_constant<int, 1>{}, yes{}) : f(integral_constant<int, 1>{}, no{});
 }
 
-cudaError_t configure_collect_smem(int cpt, size_t bytes) {
+static bool is_sliced(const DevPlan &P) { return P.slice_var != nullptr; }
+
+cudaError_t configure_collect_smem(int cpt, bool sliced, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  auto set = [&](const void *f) { return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); };
-  cudaError_t e = cpt == 8   ? set((const void *)k_collect<8>)
-                  : cpt == 4 ? set((const void *)k_collect<4>)
-                  : cpt == 2 ? set((const void *)k_collect<2>)
-                             : set((const void *)k_collect<1>);
-  if (e != cudaSuccess) return e;
-  if (cpt == 8) return set((const void *)k_collect_flow<8>);
-  if (cpt == 4) return set((const void *)k_collect_flow<4>);
-  if (cpt == 2) return set((const void *)k_collect_flow<2>);
-  return set((const void *)k_collect_flow<1>);
+  return with_collect(cpt, sliced, [&](auto c, auto sl) {
+    constexpr int CPT = decltype(c)::value;
+    constexpr bool SL = decltype(sl)::value;
+    const cudaError_t e =
+        cudaFuncSetAttribute((const void *)k_collect<CPT, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)k_collect_flow<CPT, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+  });
 }
 
 void launch_collect(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, int max_maps,
                     cudaStream_t s) {
   if (n <= 0) return;
-  if (cpt == 8) collect_t<8>(P, A, b, n, max_maps, s);
-  else if (cpt == 4) collect_t<4>(P, A, b, n, max_maps, s);
-  else if (cpt == 2) collect_t<2>(P, A, b, n, max_maps, s);
-  else collect_t<1>(P, A, b, n, max_maps, s);
+  with_collect(cpt, is_sliced(P), [&](auto c, auto sl) {
+    constexpr int CPT = decltype(c)::value;
+    const int nw = collect_warps(CPT, max_maps);
+    const size_t smem = (size_t)nw * collect_warp_smem(CPT, max_maps);
+    dim3 grid((unsigned)((n + nw - 1) / nw), (unsigned)A.tiles);
+    k_collect<CPT, decltype(sl)::value><<<grid, 32 * nw, smem, s>>>(P, A, b, n, max_maps);
+  });
 }
 
 void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, cudaStream_t s) {
@@ -967,18 +978,13 @@ void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, 
   else k_distribute<1><<<grid, kThreads, 0, s>>>(P, A, b, n);
 }
 
-template <int CPT>
-static void collect_flow_t(const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s) {
-  const int nw = collect_warps(CPT, max_maps);
-  const size_t smem = (size_t)nw * collect_warp_smem(CPT, max_maps);
-  k_collect_flow<CPT><<<blocks, 32 * nw, smem, s>>>(P, A, max_maps);
-}
-
 void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s) {
-  if (cpt == 8) collect_flow_t<8>(P, A, blocks, max_maps, s);
-  else if (cpt == 4) collect_flow_t<4>(P, A, blocks, max_maps, s);
-  else if (cpt == 2) collect_flow_t<2>(P, A, blocks, max_maps, s);
-  else collect_flow_t<1>(P, A, blocks, max_maps, s);
+  with_collect(cpt, is_sliced(P), [&](auto c, auto sl) {
+    constexpr int CPT = decltype(c)::value;
+    const int nw = collect_warps(CPT, max_maps);
+    const size_t smem = (size_t)nw * collect_warp_smem(CPT, max_maps);
+    k_collect_flow<CPT, decltype(sl)::value><<<blocks, 32 * nw, smem, s>>>(P, A, max_maps);
+  });
 }
 
 void launch_distribute_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, cudaStream_t s) {
@@ -999,14 +1005,13 @@ static int occupancy_of(K kernel, int threads, size_t smem) {
   return n > 0 ? n : 1;
 }
 
-int flow_blocks_per_sm(int cpt, bool collect, int max_maps) {
+int flow_blocks_per_sm(int cpt, bool collect, bool sliced, int max_maps) {
   if (collect) {
     const int nw = collect_warps(cpt, max_maps);
     const size_t smem = (size_t)nw * collect_warp_smem(cpt, max_maps);
-    if (cpt == 8) return occupancy_of(k_collect_flow<8>, 32 * nw, smem);
-    if (cpt == 4) return occupancy_of(k_collect_flow<4>, 32 * nw, smem);
-    if (cpt == 2) return occupancy_of(k_collect_flow<2>, 32 * nw, smem);
-    return occupancy_of(k_collect_flow<1>, 32 * nw, smem);
+    return with_collect(cpt, sliced, [&](auto c, auto sl) {
+      return occupancy_of(k_collect_flow<decltype(c)::value, decltype(sl)::value>, 32 * nw, smem);
+    });
   }
   if (cpt == 8) return occupancy_of(k_distribute_flow<8>, kThreads, 0);
   if (cpt == 4) return occupancy_of(k_distribute_flow<4>, kThreads, 0);

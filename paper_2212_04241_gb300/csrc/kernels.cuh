@@ -84,8 +84,9 @@ void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cas
 size_t collect_smem_bytes(int cpt, int max_maps);        // block (capped at kCollectSmemLimit)
 size_t collect_warp_smem_bytes(int cpt, int max_maps);   // one warp
 constexpr size_t kCollectSmemLimit = 220 * 1024;
-// raise the dynamic shared-memory limit of the collect kernel (once per plan)
-cudaError_t configure_collect_smem(int cpt, size_t bytes);
+// raise the dynamic shared-memory limit of the collect kernels (once per
+// plan; `sliced`: the instantiation for plans specialised to an observed set)
+cudaError_t configure_collect_smem(int cpt, bool sliced, size_t bytes);
 // the log P(e) kernel keeps one word per component tree in shared memory
 size_t logpe_smem_bytes(int n_comp);
 cudaError_t configure_logpe_smem(int n_comp);
@@ -93,7 +94,7 @@ constexpr int kMaxTilesPerChunk = 16384;
 // dataflow schedule: one persistent launch per pass (blocks = SMs x resident blocks per SM)
 void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s);
 void launch_distribute_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, cudaStream_t s);
-int flow_blocks_per_sm(int cpt, bool collect, int max_maps);
+int flow_blocks_per_sm(int cpt, bool collect, bool sliced, int max_maps);
 
 // plain FP64 path
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,
