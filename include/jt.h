@@ -141,6 +141,18 @@ typedef struct {
                                  JT_CASE_BAD_EVIDENCE.  NULL / 0 = none.
                                  Read during jt_compile only.  Sliced plans
                                  support every call except jt_infer_plain. */
+  int32_t rescale;            /* batched path: 1 (default) = every upward
+                                 message is scaled by 2^-k, k the exponent of
+                                 its largest entry for the case, before the
+                                 parent absorbs it, and the k are added back
+                                 into log P(e) (exact in binary floating
+                                 point; keeps deep trees and strong evidence
+                                 inside FP32's range); 0 = messages are used
+                                 as computed, so a case whose messages
+                                 underflow FP32 reports JT_CASE_ZERO_EVIDENCE
+                                 or loses accuracy (for comparison with the
+                                 unscaled definition).  The plain FP64 path
+                                 never rescales. */
 } jt_compile_opts;
 
 typedef struct {

@@ -246,6 +246,7 @@ extern "C" void jt_default_opts(jt_compile_opts *o) {
   o->max_clique_entries = 0;
   o->arena_bytes = 0;
   o->use_graphs = 1;
+  o->rescale = 1;
 }
 
 template <class T>
@@ -300,6 +301,7 @@ static jt_status upload_plan(jt_plan *pl) {
   D.d_need = reinterpret_cast<const uint32_t *>(b + o_dn);
   D.slice_var = P.n_sliced > 0 ? reinterpret_cast<const int32_t *>(b + o_sv) : nullptr;
   D.n_flow_layers = P.height + 1;
+  D.rescale = P.opts.rescale;
   D.wait_limit_ns = 1000ull * (uint64_t)(P.opts.wait_limit_us > 0 ? P.opts.wait_limit_us : 2000000);
   D.n_pgroups = (int32_t)P.pgroup_ptr.size() - 1;
   D.n_vars = P.n;

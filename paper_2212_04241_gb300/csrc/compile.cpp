@@ -672,6 +672,10 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     err = "schedule must be JT_SCHEDULE_DATAFLOW or JT_SCHEDULE_LAYERS";
     return JT_EINVAL;
   }
+  if (opts.rescale != 0 && opts.rescale != 1) {
+    err = "rescale must be 0 or 1";
+    return JT_EINVAL;
+  }
   P.tile = 32 * P.cpt_per_thread;
   // distribute tasks: children first (ascending), then owned posteriors
   std::vector<std::vector<int>> tasks_of(m);

@@ -354,7 +354,8 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
       const int c = col_of<CPT>(lane, k);
-      mval[i * W + c] = child ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]))
+      mval[i * W + c] = child ? (P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]))
+                                           : 1.f)
                               : (float)A.ev[((int64_t)tile * P.n_vars + mp.src) * W + c];
     }
   }
@@ -490,7 +491,7 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
   unsigned *mb = A.maxbits + ((int64_t)tile * P.n_cliques + it.task) * W;
 #pragma unroll
   for (int k = 0; k < CPT; ++k)
-    if (mx.x[k] > 0.f) atomicMax(mb + col_of<CPT>(lane, k), __float_as_uint(mx.x[k]));
+    if (P.rescale && mx.x[k] > 0.f) atomicMax(mb + col_of<CPT>(lane, k), __float_as_uint(mx.x[k]));
 }
 
 template <int CPT, bool SLICED>
@@ -524,7 +525,7 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
   Vec<CPT> rs;
 #pragma unroll
   for (int k = 0; k < CPT; ++k)
-    rs.x[k] = root ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + col_of<CPT>(lane, k)]))
+    rs.x[k] = root && P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + col_of<CPT>(lane, k)]))
                    : 1.f;
   const int32_t *__restrict__ At = P.ipool + T.A_off;
   const int32_t *__restrict__ sAt = P.ipool + T.sA_off;
@@ -769,7 +770,7 @@ __global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *_
     if (z > 0.f) lz += log((double)z); else zero = 1;
     K += D.comp_base_exp;
   }
-  for (int k = slice; k < P.n_comp_cliques; k += kLogpeSlices) {
+  for (int k = slice; P.rescale && k < P.n_comp_cliques; k += kLogpeSlices) {
     if (!((s_obs[P.comp_owner[k]] >> c) & 1u)) continue;
     K += pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + P.comp_cliques[k]) * W + col]);
   }

@@ -45,7 +45,7 @@ struct DevPlan {
   int32_t n_vars;
   int32_t n_cliques;
   int32_t root;
-  int32_t pad0;
+  int32_t rescale;           // 1: messages scaled by 2^-k (k per case and message)
   int64_t psi_rows;          // rows of one tile's psi region (sum |C|)
   int64_t sep_rows;          // rows of one tile's message regions
   int64_t post_rows;         // rows of one tile's posterior region (sum card)

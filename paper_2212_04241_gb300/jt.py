@@ -34,7 +34,8 @@ class CompileOpts(ctypes.Structure):
                 ("use_graphs", ctypes.c_int32), ("items_per_tile", ctypes.c_int32),
                 ("items_per_tile_distribute", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("wait_limit_us", ctypes.c_int32), ("stall_clique", ctypes.c_int32),
-                ("n_observed_set", ctypes.c_int32), ("observed_set", ctypes.c_void_p)]
+                ("n_observed_set", ctypes.c_int32), ("observed_set", ctypes.c_void_p),
+                ("rescale", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -147,7 +148,7 @@ def autotune(net, n_cases: int, **opts):
                            int(n_cases), ctypes.byref(best), ctypes.byref(ns)))
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
                                            "items_per_tile_distribute", "use_graphs", "arena_bytes",
-                                           "max_clique_entries", "schedule")}
+                                           "max_clique_entries", "schedule", "rescale")}
     if opts.get("observed_set") is not None:
         out["observed_set"] = list(opts["observed_set"])
     return out, ns.value

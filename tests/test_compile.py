@@ -161,6 +161,16 @@ def test_schedule_option():
     assert e.value.status == J.JT_EINVAL
 
 
+def test_rescale_option():
+    net = configs.network("bn20")
+    assert J.default_opts().rescale == 1                 # power-of-two rescaling by default
+    J.Plan(net, host_only=1, rescale=0)
+    for bad in (2, -1):
+        with pytest.raises(J.JTError) as e:
+            J.Plan(net, host_only=1, rescale=bad)
+        assert e.value.status == J.JT_EINVAL
+
+
 def test_observed_set_option():
     """A plan specialised to an observed set leaves those variables out of
     every clique and separator table: the tables shrink by the product of

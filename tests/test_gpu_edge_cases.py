@@ -116,6 +116,56 @@ def test_deep_chain_against_forward_backward(schedule):
             assert np.max(np.abs(got - np.stack(marg))) <= POST_TOL32
 
 
+def _least_likely_chain_evidence(net, n):
+    """Every variable of a chain observed, each in the state its CPT row
+    (given the previous variable's state) makes least likely."""
+    x = np.zeros(n, dtype=np.int32)
+    x[0] = int(np.argmin(net.cpt_of(0).reshape(-1)))
+    for v in range(1, n):
+        x[v] = int(np.argmin(net.cpt_of(v)[x[v - 1]]))
+    return x
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_rescaling_keeps_fp32_in_range(schedule):
+    """rescale=1 (default) against rescale=0 on a 400-variable chain whose
+    every variable is observed in its least likely state: log P(e) (a sum of
+    logs of CPT entries, Section 1's query at a full assignment) is far below
+    FP32's smallest subnormal (about -103 in natural log) even after each
+    clique's base table is scaled to a maximum in [1, 2), so unscaled
+    messages lose the case while scaled ones reproduce the closed form."""
+    rng = np.random.default_rng(23)
+    n, r = 400, 3
+    net = make_network(n, [r] * n, [[]] + [[v - 1] for v in range(1, n)], 1.0, rng)
+    x = _least_likely_chain_evidence(net, n)
+    expect = np.log(net.cpt_of(0).reshape(-1)[x[0]]) + sum(np.log(net.cpt_of(v)[x[v - 1], x[v]]) for v in range(1, n))
+    # upper bound of the unscaled root total: each clique's factor is at most
+    # 2 x (entry / row maximum) once its base table is scaled into [1, 2)
+    bound = np.log(2.0 * net.cpt_of(0).reshape(-1)[x[0]] / net.cpt_of(0).max())
+    bound += sum(np.log(2.0 * net.cpt_of(v)[x[v - 1], x[v]] / net.cpt_of(v).max()) for v in range(1, n))
+    assert bound < -200.0
+    ev = np.stack([x, x])
+    lp, post, st = J.Plan(net, schedule=schedule).infer(ev)
+    assert np.all(st == J.JT_CASE_OK)
+    assert np.all(np.abs(lp - expect) <= LOGPE_REL32 * abs(expect))
+    lp0, _, st0 = J.Plan(net, schedule=schedule, rescale=0).infer(ev)
+    lost = (st0 == J.JT_CASE_ZERO_EVIDENCE) | (np.abs(lp0 - expect) > 1.0)
+    assert np.all(lost), (st0, lp0, expect)
+
+
+@pytest.mark.parametrize("name,n_cases", [("bn20", 100), ("bn60", 400)])
+def test_rescaling_off_within_fp32_range(name, n_cases):
+    """Where no message leaves FP32's range, rescale=0 gives the oracle's
+    results too (both with and without its own rescaling)."""
+    net = configs.network(name)
+    ev = configs.evidence(name, net, n_cases=n_cases)
+    lp, post, st = J.Plan(net, rescale=0).infer(ev)
+    o = oracle.Oracle(net)
+    for rescale in (False, True):
+        olp, opost, ost = o.infer(ev, rescale=rescale, threads=16)
+        assert_parity32(lp, post, st, olp, opost, ost, where=f"{name} rescale=0 vs oracle rescale={rescale}")
+
+
 @pytest.mark.parametrize("schedule", SCHEDULES)
 def test_hub_cardinality_and_largest_clique(schedule):
     """bn110: a 60-state hub variable in 44 families and a 1.9e6-entry

@@ -278,6 +278,22 @@ def test_schedules_bitwise_equal(name, cpt, n):
     assert np.array_equal(a[1], b[1], equal_nan=True)
 
 
+@pytest.mark.parametrize("name,n", [("bn60", 1000), ("bn110", 130)])
+def test_repeat_runs_bitwise_equal(name, n):
+    """Every reduction has a fixed order (split segments add their pieces in
+    piece order; per-case maxima are integer maxima), so results repeat
+    bitwise: the same plan run twice, and a second plan of the same network."""
+    net = configs.network(name)
+    ev = configs.evidence(name, net, n_cases=n, seed=5)
+    p = J.Plan(net)
+    a = p.infer(ev)
+    b = p.infer(ev)
+    c = J.Plan(net).infer(ev)
+    for x in (b, c):
+        assert np.array_equal(a[2], x[2]) and np.array_equal(a[0], x[0])
+        assert np.array_equal(a[1], x[1], equal_nan=True)
+
+
 def test_expired_wait_reports_timeout_and_context_stays_usable():
     """A dataflow wait that can never be satisfied (a producer that does not
     exist, set by the testing option stall_clique) expires after the plan's
