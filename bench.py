@@ -14,6 +14,9 @@ Reported on one JSON line (rank 0):
   roofline    the dominant kernel's achieved algorithmic GB/s vs measured HBM peak
   plain_gpu   the plain per-case FP64 GPU path on a sample of the same cases
   cpu_baseline the FP64 oracle on the host cores on a bounded sample
+  cpu_layer_parallel  context: the paper's own multi-core CPU design
+              (jt_infer_cpu: one case at a time, each tree layer one parallel
+              loop over its table entries), best thread count of a sweep
   accuracy    sampled outputs of the timed run against the FP64 oracle
 
 ``--impl reference`` times the FP64 oracle (the reference arm for this build)
@@ -55,6 +58,28 @@ MEASURED_TRAFFIC = {
     ("bn60", 4096, 192, "eadfec14681946f5"): 2080268288,
     ("bn60", 4096, 384, "eadfec14681946f5"): 2058157824,
 }
+
+
+def _cpu_layers_rate(plan, ev, seconds=1.5):
+    """jt_infer_cpu (the paper's design on the host cores) over a sweep of
+    thread counts, as the paper picks its best thread count; each count
+    runs a bounded sample of the workload's cases."""
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    plan.infer_cpu(ev[:1], threads=cores)
+    one = max(time.perf_counter() - t0, 1e-6)
+    m = int(max(1, min(len(ev), seconds / one)))
+    sweep = {}
+    for t in sorted({1, 2, 4, 8, 16, 32, cores}):
+        if t > cores or m * one * cores / t > 10.0:   # bound the sweep's host time
+            continue
+        t0 = time.perf_counter()
+        plan.infer_cpu(ev[:m], threads=t)
+        sweep[t] = m / (time.perf_counter() - t0)
+    best = max(sweep, key=sweep.get)
+    return {"value": sweep[best], "unit": "cases/s", "threads": best, "cores": cores,
+            "sweep": {str(k): round(v, 2) for k, v in sweep.items()}, "dtype": "f64",
+            "sample": f"first {m} cases per thread count"}
 
 
 def _kernel_source_hash():
@@ -281,6 +306,8 @@ def main():
     ap.add_argument("--cases", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-layers", action="store_true",
+                    help="skip the multi-core CPU comparator in the paper's layer-parallel style")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix latency measurement")
     ap.add_argument("--no-autotune", action="store_true", help="default plan options instead of jt_autotune")
     ap.add_argument("--observed-set", type=int, default=0,
@@ -453,6 +480,10 @@ def main():
         cpu = {"value": rate, "unit": "cases/s", "cores": cores, "kind": "oracle",
                "sample": f"{done} cases of the workload in {dt:.1f} s"}
 
+    cpu_layers = None
+    if rank == 0 and not args.no_cpu_layers and not observed_set:
+        cpu_layers = _cpu_layers_rate(plan, ev)
+
     serving = None
     if rank == 0 and not args.no_serving and world == 1:
         serving = run_serving()
@@ -479,7 +510,7 @@ def main():
                    "parallelism": f"cases sharded, {world} rank(s)"},
         "gpu_launches": int(launches * args.steps),
         "roofline": roofline, "clocks": clock_info, "e2e": e2e, "plain_gpu": plain,
-        "cpu_baseline": cpu, "accuracy": accuracy, "serving": serving,
+        "cpu_baseline": cpu, "cpu_layer_parallel": cpu_layers, "accuracy": accuracy, "serving": serving,
     }
     print(json.dumps(line), flush=True)
     return 0

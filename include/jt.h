@@ -271,6 +271,23 @@ JT_API jt_status jt_infer_plain(jt_plan *plan, int32_t n_cases, const int32_t *e
                          void *cuda_stream);
 
 /*
+ * Multi-core CPU comparator in the style of the paper's own design
+ * (Section 2's hybrid inter- and intra-clique parallelism): on the HOST
+ * cores, one case at a time, the tree walked layer by layer with cliques
+ * and separators as the layers' nodes, every table entry of a layer one
+ * task of a single parallel loop split statically over n_threads threads
+ * (0 = the hardware's thread count), index mappings from each entry's
+ * mixed-radix digits, FP64 tables without rescaling (P(e) below FP64's
+ * range reports JT_CASE_ZERO_EVIDENCE).  For context measurements of that
+ * design on the host; results do not depend on n_threads.  HOST buffers
+ * laid out as for jt_infer; synchronous.  Runs on host_only plans too (it
+ * needs no GPU); plans specialised to an observed set get JT_EINVAL.
+ */
+JT_API jt_status jt_infer_cpu(const jt_plan *plan, int32_t n_cases, const int32_t *evidence,
+                              double *log_pe, double *posteriors, int32_t *case_status,
+                              int32_t n_threads);
+
+/*
  * Instrumented run of jt_infer_device (device buffers, same arguments) for
  * measurement: the pass launches (one per pass in the dataflow schedule,
  * one per layer in the layer schedule) are issued one by one (no graph)

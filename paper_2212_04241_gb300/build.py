@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libjt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_UNITS = ["kernels.cu", "capi.cu", "serve.cu", "noalloc.cu"]
-CXX_UNITS = ["compile.cpp"]
+CXX_UNITS = ["compile.cpp", "cpu_layers.cpp"]
 
 
 def _nvcc() -> str:
@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for u in CXX_UNITS:
         o = os.path.join(OUT_DIR, u + f".{tag}.o")
         objs.append(o)
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-c",
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-pthread", "-c",
                      os.path.join(SRC, u), "-o", o])
 
     def run(cmd):

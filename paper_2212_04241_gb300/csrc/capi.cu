@@ -653,6 +653,14 @@ static jt_status plain_case(jt_plan *pl, const int32_t *h_ev, double *d_lp, doub
   return JT_OK;
 }
 
+extern "C" jt_status jt_infer_cpu(const jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp,
+                                  double *post, int32_t *cst, int32_t n_threads) {
+  if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
+  if (n_cases == 0) return JT_OK;
+  if (!ev || !lp || !post || !cst) { set_error("null buffer"); return JT_EINVAL; }
+  return cpu_layers_infer(pl->P, n_cases, ev, lp, post, cst, n_threads);
+}
+
 extern "C" jt_status jt_infer_plain(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp,
                                     double *post, int32_t *cst, void *stream) {
   if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }

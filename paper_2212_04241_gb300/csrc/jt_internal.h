@@ -203,4 +203,8 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
 
 void set_error(const std::string &msg);
 
+// cpu_layers.cpp: the multi-core CPU comparator (jt_infer_cpu)
+jt_status cpu_layers_infer(const Plan &P, int32_t n_cases, const int32_t *ev, double *log_pe, double *post,
+                           int32_t *status, int threads);
+
 }  // namespace jt

@@ -54,7 +54,8 @@ class PlanInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["jt_default_opts", "jt_compile", "jt_autotune", "jt_infer", "jt_infer_device", "jt_infer_plain", "jt_profile",
+EXPORTS = ["jt_default_opts", "jt_compile", "jt_autotune", "jt_infer", "jt_infer_device", "jt_infer_plain", "jt_infer_cpu",
+           "jt_profile",
            "jt_plan_info", "jt_plan_clique", "jt_plan_free", "jt_status_string", "jt_last_error",
            "jt_server_create", "jt_server_add_plan", "jt_submit", "jt_poll", "jt_server_drain",
            "jt_server_stats", "jt_server_destroy"]
@@ -73,6 +74,7 @@ def _load():
         "jt_infer": ([P, I32, P, P, P, P, P], ctypes.c_int),
         "jt_infer_device": ([P, I32, P, P, P, P, P], ctypes.c_int),
         "jt_infer_plain": ([P, I32, P, P, P, P, P], ctypes.c_int),
+        "jt_infer_cpu": ([P, I32, P, P, P, P, I32], ctypes.c_int),
         "jt_profile": ([P, I32, P, P, P, P, P, P], ctypes.c_int),
         "jt_plan_info": ([P, ctypes.POINTER(PlanInfo)], ctypes.c_int),
         "jt_plan_clique": ([P, I32, P, P, P, P], ctypes.c_int),
@@ -227,6 +229,15 @@ class Plan:
         assert ev.shape[1] == self.n
         lp, post, st = self._outputs(ev.shape[0])
         _check(lib.jt_infer_plain(self._h, ev.shape[0], _ptr(ev), _ptr(lp), _ptr(post), _ptr(st), stream))
+        return lp, post, st
+
+    def infer_cpu(self, evidence, threads=0):
+        """Multi-core CPU comparator in the paper's layer-parallel style, host
+        buffers (jt_infer_cpu); threads = 0 uses every hardware thread."""
+        ev = np.ascontiguousarray(np.atleast_2d(evidence), dtype=np.int32)
+        assert ev.shape[1] == self.n
+        lp, post, st = self._outputs(ev.shape[0])
+        _check(lib.jt_infer_cpu(self._h, ev.shape[0], _ptr(ev), _ptr(lp), _ptr(post), _ptr(st), int(threads)))
         return lp, post, st
 
     def infer_device(self, d_evidence, d_log_pe, d_post, d_status, n_cases=None, stream=None):
