@@ -60,6 +60,19 @@ MEASURED_TRAFFIC = {
 }
 
 
+def _kept_columns(net, roots):
+    """Posterior columns of the variables a plan pruned to a query set keeps:
+    the query and observed sets and their ancestors."""
+    keep, stack = set(), list(roots)
+    while stack:
+        v = stack.pop()
+        if v not in keep:
+            keep.add(v)
+            stack.extend(int(p) for p in net.parents_of(v))
+    offs = np.concatenate([[0], np.cumsum(net.card)])
+    return np.concatenate([np.arange(offs[v], offs[v + 1]) for v in sorted(keep)])
+
+
 def _cpu_layers_rate(plan, ev, seconds=1.5):
     """jt_infer_cpu (the paper's design on the host cores) over a sweep of
     thread counts, as the paper picks its best thread count; each count
@@ -313,6 +326,9 @@ def main():
     ap.add_argument("--observed-set", type=int, default=0,
                     help="K > 0: every case observes the same K variables (seeded choice, states from an "
                     "ancestral sample) and the plan is specialised to that set")
+    ap.add_argument("--query-set", type=int, default=0,
+                    help="Q > 0 (with --observed-set): the plan is also pruned to Q query variables (seeded choice "
+                    "outside the observed set); the barren variables are removed")
     ap.add_argument("--plan", default="", help="fixed plan options as JSON (e.g. '{\"items_per_tile\": 96}'), "
                     "instead of jt_autotune")
     ap.add_argument("--serving-only", action="store_true", help="only the serving-mix measurement")
@@ -338,6 +354,13 @@ def main():
         x = sample_cases(net, n_cases, 1.0, seed=rank_evidence_seed(name, rank))
         ev = np.full_like(x, -1, dtype=np.int32)
         ev[:, observed_set] = x[:, observed_set]
+    query_set = None
+    if args.query_set > 0:
+        if not observed_set:
+            raise SystemExit("--query-set needs --observed-set")
+        rng = np.random.default_rng(4321)
+        rest = [v for v in range(net.n) if v not in observed_set]
+        query_set = sorted(int(v) for v in rng.choice(rest, size=args.query_set, replace=False))
 
     if args.impl == "reference":
         return run_reference(args, name, net, ev, rank, world)
@@ -355,6 +378,8 @@ def main():
     import paper_2212_04241_gb300.jt as J
     # the library's autotuner picks the tile shape for this network and batch
     spec = {"observed_set": observed_set} if observed_set else {}
+    if query_set:
+        spec["query_set"] = query_set
     if args.plan:
         tuned = dict(json.loads(args.plan), **spec)
     else:
@@ -412,9 +437,10 @@ def main():
         idx = np.random.default_rng(0).choice(n_cases, size=min(64, n_cases), replace=False)
         olp, opost, ost = oracle.Oracle(net).infer(ev[idx], threads=os.cpu_count() or 1)
         ok = ost == 0
+        cols = _kept_columns(net, query_set + observed_set) if query_set else np.arange(plan.sum_card)
         accuracy = {
             "sample_cases": int(len(idx)),
-            "max_abs_posterior_err": float(np.max(np.abs(post[idx][ok] - opost[ok]))),
+            "max_abs_posterior_err": float(np.max(np.abs(post[idx][ok][:, cols] - opost[ok][:, cols]))),
             "max_rel_logpe_err": float(np.max(np.abs(lp[idx][ok] - olp[ok]) / np.maximum(1, np.abs(olp[ok])))),
             "status_match": bool(np.array_equal(st[idx], ost)),
         }
@@ -437,7 +463,7 @@ def main():
     # the plan's distribute work-item target (0 in the options = items_per_tile, whose 0 = 192)
     items_d = int(tuned.get("items_per_tile_distribute") or tuned.get("items_per_tile") or 192)
     traffic = (MEASURED_TRAFFIC.get((name, n_cases, items_d, _kernel_source_hash()))
-               if dataflow and dom == "distribute" else None)
+               if dataflow and dom == "distribute" and not observed_set else None)
     roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "launches": prof[f"{dom}_launches"],
@@ -464,7 +490,7 @@ def main():
                "d2h_bytes_per_step": int(n_cases * (8 + 8 * plan.sum_card + 4)), "ms_per_step": dt * 1e3}
 
     plain = None
-    if rank == 0 and not args.no_plain:
+    if rank == 0 and not args.no_plain and not observed_set:
         m = min(n_cases, 64 if name in ("bn20", "bn60", "bn1000") else 8)
         plan.infer_plain(ev[:2])
         t0 = time.perf_counter()
@@ -498,8 +524,9 @@ def main():
         "value": value, "unit": "cases/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[name] + (f"_observedset{args.observed_set}" if observed_set else ""),
-                   "observed_set": observed_set, "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
+        "config": {"workload": WORKLOADS[name] + (f"_observedset{args.observed_set}" if observed_set else "")
+                   + (f"_queryset{args.query_set}" if query_set else ""),
+                   "observed_set": observed_set, "query_set": query_set, "pruned_vars": info["pruned_vars"], "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
                    "chunk_cases": info["chunk_cases"], "levels": info["n_levels"],
                    "autotuned": ({k: tuned.get(k) for k in ("cases_per_thread", "items_per_tile", "items_per_tile_distribute")}
                                  if tuned and not args.plan and not args.no_autotune else None),

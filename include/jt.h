@@ -153,10 +153,30 @@ typedef struct {
                                  or loses accuracy (for comparison with the
                                  unscaled definition).  The plain FP64 path
                                  never rescales. */
+  int32_t n_query_set;        /* prune the plan to a query set: */
+  const int32_t *query_set;   /* n_query_set distinct variables whose
+                                 posteriors the plan must answer.  The plan
+                                 keeps only these, the variables of
+                                 observed_set, and their ancestors; every
+                                 other variable is barren (no kept variable
+                                 depends on it, so summing it out of its CPT
+                                 gives exactly 1) and is removed from the
+                                 network before the tree is built.  P(e) and
+                                 the posteriors of every kept variable are
+                                 unchanged; the posterior columns of removed
+                                 variables are NaN; a case that observes a
+                                 removed variable gets JT_CASE_BAD_EVIDENCE.
+                                 Evidence and posterior rows keep the full
+                                 network's layout.  NULL / 0 = none.  Read
+                                 during jt_compile only.  Pruned plans
+                                 support the batched calls (jt_infer,
+                                 jt_infer_device, jt_infer_device_noalloc,
+                                 jt_profile, jt_autotune), not
+                                 jt_infer_plain, jt_infer_cpu or the server. */
 } jt_compile_opts;
 
 typedef struct {
-  int32_t n_vars;
+  int32_t n_vars;               /* variables of an evidence row (the full network) */
   int32_t n_cliques;
   int32_t n_levels;             /* tree height + 1 */
   int32_t root;
@@ -177,6 +197,7 @@ typedef struct {
                                  applied to an upward message (a separator
                                  smaller than every clique holding them)
                                  rather than evaluated per clique entry */
+  int32_t pruned_vars;          /* barren variables removed (query_set) */
 } jt_plan_info_t;
 
 /* Fill opts with the defaults listed above. */

@@ -259,6 +259,16 @@ static size_t put(std::vector<char> &blob, const std::vector<T> &v) {
 
 static jt_status upload_plan(jt_plan *pl) {
   Plan &P = pl->P;
+  // the kernels index evidence and posterior rows with these sizes
+  const bool rows_ok = P.n_pruned > 0
+                           ? (P.io_n > P.n && P.io_sum_card > P.sum_card && (int)P.io_var.size() == P.n &&
+                              (int64_t)P.io_post_col.size() == P.sum_card && (int)P.io_dropped.size() == P.io_n - P.n &&
+                              (int64_t)P.io_nan_cols.size() == P.io_sum_card - P.sum_card)
+                           : (P.io_n == P.n && P.io_sum_card == P.sum_card);
+  if (!rows_ok) {
+    set_error("internal: inconsistent evidence or posterior row layout");
+    return JT_EINVAL;
+  }
   std::vector<char> blob;
   std::vector<int32_t> card32(P.card.begin(), P.card.end());
   const size_t o_cl = put(blob, P.dcl), o_map = put(blob, P.dmap), o_task = put(blob, P.dtask);
@@ -270,6 +280,8 @@ static jt_status upload_plan(jt_plan *pl) {
   const size_t o_dfp = put(blob, P.d_flow_pref), o_dfb = put(blob, P.d_flow_begin);
   const size_t o_cn = put(blob, P.c_need), o_cno = put(blob, P.c_notify), o_dn = put(blob, P.d_need);
   const size_t o_sv = put(blob, P.slice_var);
+  const size_t o_iv = put(blob, P.io_var), o_id = put(blob, P.io_dropped);
+  const size_t o_ipc = put(blob, P.io_post_col), o_inc = put(blob, P.io_nan_cols);
   JT_CUDA_TRY(cudaMalloc(&pl->d_static, blob.size()));
   pl->static_bytes = blob.size();
   JT_CUDA_TRY(cudaMemcpy(pl->d_static, blob.data(), blob.size(), cudaMemcpyHostToDevice));
@@ -300,6 +312,15 @@ static jt_status upload_plan(jt_plan *pl) {
   D.c_notify = reinterpret_cast<const int32_t *>(b + o_cno);
   D.d_need = reinterpret_cast<const uint32_t *>(b + o_dn);
   D.slice_var = P.n_sliced > 0 ? reinterpret_cast<const int32_t *>(b + o_sv) : nullptr;
+  const bool pruned = P.n_pruned > 0;
+  D.io_var = pruned ? reinterpret_cast<const int32_t *>(b + o_iv) : nullptr;
+  D.io_dropped = pruned ? reinterpret_cast<const int32_t *>(b + o_id) : nullptr;
+  D.io_post_col = pruned ? reinterpret_cast<const int32_t *>(b + o_ipc) : nullptr;
+  D.io_nan_cols = pruned ? reinterpret_cast<const int32_t *>(b + o_inc) : nullptr;
+  D.io_post_rows = P.io_sum_card;
+  D.io_n = P.io_n;
+  D.n_dropped = (int32_t)P.io_dropped.size();
+  D.n_nan_cols = (int32_t)P.io_nan_cols.size();
   D.n_flow_layers = P.height + 1;
   D.rescale = P.opts.rescale;
   D.wait_limit_ns = 1000ull * (uint64_t)(P.opts.wait_limit_us > 0 ? P.opts.wait_limit_us : 2000000);
@@ -344,7 +365,7 @@ extern "C" jt_status jt_compile(int32_t n_vars, const int32_t *card, const int32
   std::string err;
   jt_status st;
   try {
-    st = build_plan(n_vars, card, parent_ptr, parents, cpt, o, pl->P, err);
+    st = build_plan_pruned(n_vars, card, parent_ptr, parents, cpt, o, pl->P, err);
   } catch (const std::bad_alloc &) {
     st = JT_ENOMEM;
     err = "host allocation failed while compiling";
@@ -403,22 +424,22 @@ extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
   if (!pl || !o) { set_error("null argument"); return JT_EINVAL; }
   const Plan &P = pl->P;
   std::memset(o, 0, sizeof(*o));
-  o->n_vars = P.n;
+  o->n_vars = P.io_n;
   o->n_cliques = (int32_t)P.cl.size();
   o->n_levels = P.height + 1;
   o->root = P.root;
   o->sum_clique_entries = P.sum_cl;
   o->max_clique_entries = P.max_cl;
   o->sum_sep_entries = P.sum_sep;
-  o->sum_card = P.sum_card;
+  o->sum_card = P.io_sum_card;
   o->tile_cases = P.tile;
   o->chunk_cases = pl->arena.tiles * P.tile;
   o->arena_bytes = (int64_t)pl->arena.bytes;
   o->static_device_bytes = (int64_t)pl->static_bytes;
   o->collect_items = (int64_t)P.citems.size();
   o->distribute_items = (int64_t)P.ditems.size();
-  o->algorithmic_bytes_per_case = 8.0 * (double)P.sum_cl + 16.0 * (double)P.sum_sep + 4.0 * P.n +
-                                  8.0 * (double)P.sum_card + 8.0;
+  o->algorithmic_bytes_per_case = 8.0 * (double)P.sum_cl + 16.0 * (double)P.sum_sep + 4.0 * P.io_n +
+                                  8.0 * (double)P.io_sum_card + 8.0;
   int k = 3;  // evidence + log P(e) + posteriors
   if (P.opts.schedule == JT_SCHEDULE_LAYERS) {
     for (const Level &lv : P.levels) {
@@ -430,6 +451,7 @@ extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
   }
   o->kernels_per_chunk = k;
   o->sliced_vars = P.n_sliced;
+  o->pruned_vars = P.n_pruned;
   o->separator_evidence_vars = 0;
   for (const HostClique &C : P.cl) o->separator_evidence_vars += (int32_t)C.ev_sep.size();
   return JT_OK;
@@ -440,7 +462,10 @@ extern "C" jt_status jt_plan_clique(const jt_plan *pl, int32_t c, int32_t *n_var
   if (!pl || c < 0 || c >= (int32_t)pl->P.cl.size()) { set_error("bad clique id"); return JT_EINVAL; }
   const HostClique &C = pl->P.cl[c];
   if (n_vars) *n_vars = (int32_t)C.vars.size();
-  if (vars) for (size_t i = 0; i < C.vars.size() && i < 64; ++i) vars[i] = C.vars[i];
+  // variable ids of the full network (a pruned plan renumbers its kept variables)
+  if (vars)
+    for (size_t i = 0; i < C.vars.size() && i < 64; ++i)
+      vars[i] = pl->P.n_pruned > 0 ? pl->P.io_var[C.vars[i]] : C.vars[i];
   if (parent) *parent = C.parent;
   if (depth) *depth = C.depth;
   return JT_OK;
@@ -485,7 +510,7 @@ extern "C" jt_status jt_infer_device(jt_plan *pl, int32_t n_cases, const int32_t
   const int64_t chunk = (int64_t)pl->arena.tiles * W;
   for (int64_t b = 0; b < n_cases; b += chunk) {
     const int32_t nc = (int32_t)std::min<int64_t>(chunk, n_cases - b);
-    st = run_chunk(pl, pl->arena, d_ev + b * pl->P.n, nc, d_lp + b, d_post + b * pl->P.sum_card, d_st + b, s);
+    st = run_chunk(pl, pl->arena, d_ev + b * pl->P.io_n, nc, d_lp + b, d_post + b * pl->P.io_sum_card, d_st + b, s);
     if (st != JT_OK) return st;
   }
   return JT_OK;
@@ -495,9 +520,9 @@ static jt_status ensure_io(jt_plan *pl, int cases) {
   if (pl->io_cases >= cases) return JT_OK;
   free_io(pl);
   const Plan &P = pl->P;
-  pl->io_ev = align_up(sizeof(int32_t) * (size_t)cases * P.n);
+  pl->io_ev = align_up(sizeof(int32_t) * (size_t)cases * P.io_n);
   pl->io_lp = align_up(sizeof(double) * (size_t)cases);
-  pl->io_post = align_up(sizeof(double) * (size_t)cases * P.sum_card);
+  pl->io_post = align_up(sizeof(double) * (size_t)cases * P.io_sum_card);
   pl->io_st = align_up(sizeof(int32_t) * (size_t)cases);
   const size_t bytes = pl->io_ev + pl->io_lp + pl->io_post + pl->io_st;
   JT_CUDA_TRY(cudaMalloc(&pl->d_io, bytes));
@@ -543,11 +568,11 @@ extern "C" jt_status jt_infer(jt_plan *pl, int32_t n_cases, const int32_t *ev, d
   if (pinned(ev) && pinned(lp) && pinned(post) && pinned(cst)) {
     for (int64_t b = 0; b < n_cases; b += chunk) {
       const int32_t nc = (int32_t)std::min<int64_t>(chunk, n_cases - b);
-      JT_CUDA_TRY(cudaMemcpyAsync(d_ev, ev + b * P.n, sizeof(int32_t) * (size_t)nc * P.n, cudaMemcpyHostToDevice, s));
+      JT_CUDA_TRY(cudaMemcpyAsync(d_ev, ev + b * P.io_n, sizeof(int32_t) * (size_t)nc * P.io_n, cudaMemcpyHostToDevice, s));
       st = run_chunk(pl, pl->arena, d_ev, nc, d_lp, d_po, d_st, s);
       if (st != JT_OK) return st;
       JT_CUDA_TRY(cudaMemcpyAsync(lp + b, d_lp, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
-      JT_CUDA_TRY(cudaMemcpyAsync(post + b * P.sum_card, d_po, sizeof(double) * (size_t)nc * P.sum_card,
+      JT_CUDA_TRY(cudaMemcpyAsync(post + b * P.io_sum_card, d_po, sizeof(double) * (size_t)nc * P.io_sum_card,
                                   cudaMemcpyDeviceToHost, s));
       JT_CUDA_TRY(cudaMemcpyAsync(cst + b, d_st, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, s));
     }
@@ -556,18 +581,18 @@ extern "C" jt_status jt_infer(jt_plan *pl, int32_t n_cases, const int32_t *ev, d
   }
   for (int64_t b = 0; b < n_cases; b += chunk) {
     const int32_t nc = (int32_t)std::min<int64_t>(chunk, n_cases - b);
-    std::memcpy(h_ev, ev + b * P.n, sizeof(int32_t) * (size_t)nc * P.n);
-    JT_CUDA_TRY(cudaMemcpyAsync(d_ev, h_ev, sizeof(int32_t) * (size_t)nc * P.n, cudaMemcpyHostToDevice, s));
+    std::memcpy(h_ev, ev + b * P.io_n, sizeof(int32_t) * (size_t)nc * P.io_n);
+    JT_CUDA_TRY(cudaMemcpyAsync(d_ev, h_ev, sizeof(int32_t) * (size_t)nc * P.io_n, cudaMemcpyHostToDevice, s));
     st = run_chunk(pl, pl->arena, d_ev, nc, d_lp, d_po, d_st, s);
     if (st != JT_OK) return st;
     JT_CUDA_TRY(cudaMemcpyAsync(h_lp, d_lp, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
-    JT_CUDA_TRY(cudaMemcpyAsync(h_po, d_po, sizeof(double) * (size_t)nc * P.sum_card, cudaMemcpyDeviceToHost, s));
+    JT_CUDA_TRY(cudaMemcpyAsync(h_po, d_po, sizeof(double) * (size_t)nc * P.io_sum_card, cudaMemcpyDeviceToHost, s));
     JT_CUDA_TRY(cudaMemcpyAsync(h_st, d_st, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, s));
     JT_CUDA_TRY(cudaStreamSynchronize(s));
     st = check_arena_flag(pl->arena);
     if (st != JT_OK) return st;
     std::memcpy(lp + b, h_lp, sizeof(double) * nc);
-    std::memcpy(post + b * P.sum_card, h_po, sizeof(double) * (size_t)nc * P.sum_card);
+    std::memcpy(post + b * P.io_sum_card, h_po, sizeof(double) * (size_t)nc * P.io_sum_card);
     std::memcpy(cst + b, h_st, sizeof(int32_t) * nc);
   }
   return JT_OK;
@@ -665,7 +690,10 @@ extern "C" jt_status jt_infer_plain(jt_plan *pl, int32_t n_cases, const int32_t 
                                     double *post, int32_t *cst, void *stream) {
   if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
   if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
-  if (pl->P.n_sliced > 0) { set_error("the plain path runs unspecialised plans only"); return JT_EINVAL; }
+  if (pl->P.n_sliced > 0 || pl->P.n_pruned > 0) {
+    set_error("the plain path runs unspecialised plans only");
+    return JT_EINVAL;
+  }
   if (n_cases == 0) return JT_OK;
   if (!ev || !lp || !post || !cst) { set_error("null buffer"); return JT_EINVAL; }
   std::lock_guard<std::mutex> lk(pl->mu);
@@ -747,7 +775,7 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
     A.tiles = (nc + W - 1) / W;
     JT_CUDA_TRY(cudaMemsetAsync(A.bad, 0, arena_layout(P).bad * (size_t)A.tiles, s));
     int e0 = mark();
-    launch_evidence(P.cpt_per_thread, d_ev + b * P.n, nc, pl->dp, A, s);
+    launch_evidence(P.cpt_per_thread, d_ev + b * P.io_n, nc, pl->dp, A, s);
     spans.push_back({e0, mark(), 2});
     if (P.opts.schedule != JT_SCHEDULE_LAYERS) {
       // dataflow: one span per pass (the counters are reset inside the first)
@@ -782,7 +810,7 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
     }
     int f0 = mark();
     launch_finalize(P.cpt_per_thread, pl->dp, A, nc, P.dcl[P.root].sep_row, d_lp + b,
-                    d_post + b * P.sum_card, d_st + b, s);
+                    d_post + b * P.io_sum_card, d_st + b, s);
     spans.push_back({f0, mark(), 2});
   }
   const int stop = mark();

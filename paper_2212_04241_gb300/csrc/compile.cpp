@@ -277,6 +277,15 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   P.post_off.assign(n, 0);
   P.sum_card = 0;
   for (int v = 0; v < n; ++v) { P.post_off[v] = P.sum_card; P.sum_card += card[v]; }
+  // rows of evidence and posteriors (build_plan_pruned widens them to the
+  // full network after building a pruned plan)
+  P.io_n = n;
+  P.io_sum_card = P.sum_card;
+  P.n_pruned = 0;
+  P.io_var.clear();
+  P.io_dropped.clear();
+  P.io_post_col.clear();
+  P.io_nan_cols.clear();
   // observed set of a specialised plan
   P.slice_var.assign(n, 0);
   P.n_sliced = 0;
@@ -965,6 +974,109 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   }
   P.p_root_map.assign(1, plain_map(P.cl[root], std::vector<int>{}));
   for (int v = 0; v < n; ++v) P.p_post_map[v] = plain_map(P.cl[P.post_src[v]], std::vector<int>{v});
+  return JT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// query-set pruning: the plan keeps the query set, the observed set and all
+// their ancestors.  The rest is barren: no kept variable has a removed
+// parent, so the removed variables sum out of the joint one CPT at a time
+// (children first), each sum being exactly 1, and the joint of the kept
+// variables is the product of their own CPTs (the marginalisation of
+// Section 2 applied to whole variables).
+// ---------------------------------------------------------------------------
+jt_status build_plan_pruned(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
+                            const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err) {
+  if (opts.n_query_set == 0) return build_plan(n, card, pptr, par, cpt, opts, P, err);
+  if (opts.n_query_set < 0 || opts.query_set == nullptr) {
+    err = "bad query set";
+    return JT_EINVAL;
+  }
+  jt_status st = validate(n, card, pptr, par, cpt, err);
+  if (st != JT_OK) return st;
+  if (opts.n_observed_set < 0 || (opts.n_observed_set > 0 && opts.observed_set == nullptr)) {
+    err = "bad observed set";
+    return JT_EINVAL;
+  }
+  std::vector<char> keep(n, 0), listed(n, 0);
+  std::vector<int> stack;
+  for (int i = 0; i < opts.n_query_set; ++i) {
+    const int v = opts.query_set[i];
+    if (v < 0 || v >= n || listed[v]) {
+      err = "query set: variable out of range or listed twice";
+      return JT_EINVAL;
+    }
+    listed[v] = 1;
+    stack.push_back(v);
+  }
+  for (int i = 0; i < opts.n_observed_set; ++i) {
+    const int v = opts.observed_set[i];
+    if (v < 0 || v >= n) {
+      err = "observed set: variable out of range or listed twice";
+      return JT_EINVAL;
+    }
+    stack.push_back(v);
+  }
+  while (!stack.empty()) {  // ancestral closure
+    const int v = stack.back();
+    stack.pop_back();
+    if (keep[v]) continue;
+    keep[v] = 1;
+    for (int k = pptr[v]; k < pptr[v + 1]; ++k) stack.push_back(par[k]);
+  }
+  std::vector<int32_t> sub_of(n, -1), orig;
+  for (int v = 0; v < n; ++v)
+    if (keep[v]) {
+      sub_of[v] = (int32_t)orig.size();
+      orig.push_back(v);
+    }
+  jt_compile_opts so = opts;
+  so.n_query_set = 0;
+  so.query_set = nullptr;
+  if ((int)orig.size() == n) return build_plan(n, card, pptr, par, cpt, so, P, err);  // nothing barren
+  // the kept network, variables renumbered in their original order
+  const int k = (int)orig.size();
+  std::vector<int32_t> kcard(k), kpptr(k + 1, 0), kpar;
+  std::vector<double> kcpt;
+  std::vector<int64_t> off(n + 1, 0);
+  for (int v = 0; v < n; ++v) {
+    int64_t rows = 1;
+    for (int q = pptr[v]; q < pptr[v + 1]; ++q) rows *= card[par[q]];
+    off[v + 1] = off[v] + rows * card[v];
+  }
+  for (int i = 0; i < k; ++i) {
+    const int v = orig[i];
+    kcard[i] = card[v];
+    for (int q = pptr[v]; q < pptr[v + 1]; ++q) kpar.push_back(sub_of[par[q]]);  // kept: ancestors are kept
+    kpptr[i + 1] = (int32_t)kpar.size();
+    kcpt.insert(kcpt.end(), cpt + off[v], cpt + off[v + 1]);
+  }
+  if (kpar.empty()) kpar.push_back(0);
+  std::vector<int32_t> kobs;
+  for (int i = 0; i < opts.n_observed_set; ++i) kobs.push_back(sub_of[opts.observed_set[i]]);
+  so.observed_set = kobs.empty() ? nullptr : kobs.data();
+  st = build_plan(k, kcard.data(), kpptr.data(), kpar.data(), kcpt.data(), so, P, err);
+  if (st != JT_OK) return st;
+  // rows of evidence and posteriors keep the full network's layout
+  std::vector<int64_t> full_off(n, 0);
+  int64_t sc = 0;
+  for (int v = 0; v < n; ++v) { full_off[v] = sc; sc += card[v]; }
+  P.io_n = n;
+  P.io_sum_card = sc;
+  P.n_pruned = n - k;
+  P.io_var.assign(orig.begin(), orig.end());
+  P.io_dropped.clear();
+  P.io_nan_cols.clear();
+  for (int v = 0; v < n; ++v)
+    if (!keep[v]) {
+      P.io_dropped.push_back(v);
+      for (int j = 0; j < card[v]; ++j) P.io_nan_cols.push_back((int32_t)(full_off[v] + j));
+    }
+  P.io_post_col.assign(P.sum_card, 0);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < kcard[i]; ++j) P.io_post_col[P.post_off[i] + j] = (int32_t)(full_off[orig[i]] + j);
+  P.opts.n_query_set = 0;
+  P.opts.query_set = nullptr;
   return JT_OK;
 }
 

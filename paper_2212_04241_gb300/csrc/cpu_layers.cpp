@@ -293,7 +293,7 @@ int64_t chunks(int64_t n) { return (n + kChunk - 1) / kChunk; }
 
 jt_status cpu_layers_infer(const Plan &P, int32_t n_cases, const int32_t *ev, double *log_pe, double *post,
                            int32_t *status, int threads) {
-  if (P.n_sliced > 0) {
+  if (P.n_sliced > 0 || P.n_pruned > 0) {
     set_error("the CPU comparator runs unspecialised plans only");
     return JT_EINVAL;
   }

@@ -191,6 +191,16 @@ struct Plan {
   std::vector<int64_t> p_base_off;  // per clique, offset in base64 / plain psi
   std::vector<int64_t> p_sep_off;   // per clique, offset in plain sep arrays
 
+  // pruned plan (query set): the tree is built on the kept variables only;
+  // evidence and posterior rows keep the full network's layout
+  int io_n = 0;                       // variables of a row of evidence (full network)
+  int64_t io_sum_card = 0;            // columns of a posterior row (full network)
+  int n_pruned = 0;                   // barren variables removed
+  std::vector<int32_t> io_var;        // kept variable -> its id in the full network
+  std::vector<int32_t> io_dropped;    // ids of the removed variables
+  std::vector<int32_t> io_post_col;   // kept posterior column -> full-row column
+  std::vector<int32_t> io_nan_cols;   // full-row columns of the removed variables
+
   jt_compile_opts opts{};
   int cpt_per_thread = 4;
   int tile = 128;
@@ -200,6 +210,9 @@ struct Plan {
 // compile.cpp
 jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
                      const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err);
+// build_plan on the network pruned to opts.query_set (build_plan when none)
+jt_status build_plan_pruned(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
+                            const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err);
 
 void set_error(const std::string &msg);
 

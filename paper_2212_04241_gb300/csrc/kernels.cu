@@ -216,10 +216,22 @@ __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) 
 // ---------------------------------------------------------------------------
 // A block moves 32 cases x 32 variables through shared memory, so both the
 // [case][var] reads and the [tile][var][W] writes are coalesced.  Cases of
-// the chunk's last tile beyond n_cases get -1 (unobserved).
+// the chunk's last tile beyond n_cases get -1 (unobserved).  Rows of
+// ev_in have io_n columns (the full network of a pruned plan); the blocks
+// past the kept variables check that the removed ones are unobserved.
 __global__ void k_evidence(const int32_t *__restrict__ ev_in, int32_t n_cases, DevPlan P, DevArena A, int W) {
   __shared__ int32_t t[32][33];
   const int64_t c0 = (int64_t)blockIdx.x * 32;
+  const int nvb = (P.n_vars + 31) / 32;
+  if ((int)blockIdx.y >= nvb) {
+    const int k = ((int)blockIdx.y - nvb) * 32 + threadIdx.x;
+    if (k < P.n_dropped)
+      for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i;
+        if (c < n_cases && ev_in[c * P.io_n + P.io_dropped[k]] != -1) A.bad[c] = 1;
+      }
+    return;
+  }
   const int v0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int64_t c = c0 + i;
@@ -229,7 +241,7 @@ __global__ void k_evidence(const int32_t *__restrict__ ev_in, int32_t n_cases, D
     // valid state (0 stands in where a case breaks the contract or pads the tile)
     const bool in_set = P.slice_var != nullptr && v < P.n_vars && P.slice_var[v] != 0;
     if (v < P.n_vars && c < n_cases) {
-      val = ev_in[c * P.n_vars + v];
+      val = ev_in[c * P.io_n + (P.io_var ? P.io_var[v] : v)];
       if (val < -1 || val >= P.card[v] || (in_set && val < 0)) {
         A.bad[c] = 1;
         val = -1;
@@ -804,6 +816,13 @@ __global__ void k_posterior(DevPlan P, DevArena A, int W, int32_t n_cases, const
   const int64_t cs = (int64_t)tile * W + c;
   const int64_t left = (int64_t)n_cases - (int64_t)tile * W;
   const int rows_here = (int)(left < W ? left : W);
+  if ((int)blockIdx.y >= P.n_pgroups) {  // pruned plan: columns of the removed variables
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int rr = warp; rr < rows_here; rr += nw)
+      for (int k = lane; k < P.n_nan_cols; k += 32)
+        post[((int64_t)tile * W + rr) * P.io_post_rows + P.io_nan_cols[k]] = NAN;
+    return;
+  }
   const int st = cs < n_cases ? status[cs] : JT_CASE_BAD_EVIDENCE;
   const int v0 = P.pgroup_ptr[blockIdx.y], v1 = P.pgroup_ptr[blockIdx.y + 1];
   int64_t col0 = P.post_off[v0];  // first column of the staged block
@@ -812,7 +831,8 @@ __global__ void k_posterior(DevPlan P, DevArena A, int W, int32_t n_cases, const
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int rr = warp; rr < rows_here; rr += nw)
       for (int j = lane; j < ncols; j += 32)
-        post[((int64_t)tile * W + rr) * P.post_rows + col0 + j] = stage[rr * (kStageCols + 1) + j];
+        post[((int64_t)tile * W + rr) * P.io_post_rows + (P.io_post_col ? P.io_post_col[col0 + j] : col0 + j)] =
+            stage[rr * (kStageCols + 1) + j];
     __syncthreads();
   };
   for (int v = v0; v < v1; ++v) {
@@ -919,7 +939,8 @@ size_t collect_warp_smem_bytes(int cpt, int max_maps) { return collect_warp_smem
 void launch_evidence(int cpt, const int32_t *d_ev_in, int32_t n_cases, const DevPlan &P,
                      const DevArena &A, cudaStream_t s) {
   const int W = 32 * cpt;
-  const dim3 grid((unsigned)(((int64_t)A.tiles * W + 31) / 32), (unsigned)((P.n_vars + 31) / 32));
+  const dim3 grid((unsigned)(((int64_t)A.tiles * W + 31) / 32),
+                  (unsigned)((P.n_vars + 31) / 32 + (P.n_dropped + 31) / 32));
   k_evidence<<<grid, dim3(32, 8), 0, s>>>(d_ev_in, n_cases, P, A, W);
 }
 
@@ -1062,7 +1083,8 @@ void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cas
   const size_t lsmem = logpe_smem_bytes(P.n_comp);
   k_logpe<<<(unsigned)((n_cases + 31) / 32), dim3(32, kLogpeSlices), lsmem, s>>>(P, A, W, n_cases, d_log_pe, d_status);
   const size_t smem = sizeof(double) * (size_t)W * (kStageCols + 1);
-  k_posterior<<<dim3(tiles, (unsigned)P.n_pgroups), W, smem, s>>>(P, A, W, n_cases, d_status, d_post);
+  k_posterior<<<dim3(tiles, (unsigned)(P.n_pgroups + (P.n_nan_cols > 0))), W, smem, s>>>(P, A, W, n_cases,
+                                                                                         d_status, d_post);
 }
 
 }  // namespace jt

@@ -51,6 +51,16 @@ struct DevPlan {
   int64_t post_rows;         // rows of one tile's posterior region (sum card)
   int64_t n_partials;
   int64_t n_groups;
+  // plan pruned to a query set: rows of evidence and posteriors keep the
+  // full network's layout (identity maps when nothing was pruned)
+  const int32_t *io_var;       // [n_vars] evidence column of each kept variable; nullptr: identity
+  const int32_t *io_dropped;   // [n_dropped] evidence columns that must stay unobserved
+  const int32_t *io_post_col;  // [post_rows] output column of each posterior column; nullptr: identity
+  const int32_t *io_nan_cols;  // [n_nan_cols] output columns of removed variables (NaN)
+  int64_t io_post_rows;        // output columns per case
+  int32_t io_n;                // evidence columns per case
+  int32_t n_dropped;
+  int32_t n_nan_cols;
 };
 
 // Per-batch device memory.  Row-major [tile][row][W] for the FP32 tables,

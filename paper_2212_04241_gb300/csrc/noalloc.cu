@@ -95,9 +95,9 @@ extern "C" jt_status jt_infer_device_noalloc(jt_plan *pl, int32_t n_cases, const
     DevArena A = a.da;
     A.tiles = (nc + W - 1) / W;
     cudaMemsetAsync(A.bad, 0, L.bad * (size_t)A.tiles, s);
-    launch_evidence(P.cpt_per_thread, d_ev + b * P.n, nc, pl->dp, A, s);
+    launch_evidence(P.cpt_per_thread, d_ev + b * P.io_n, nc, pl->dp, A, s);
     enqueue_passes(pl, A, s);
-    launch_finalize(P.cpt_per_thread, pl->dp, A, nc, P.dcl[P.root].sep_row, d_lp + b, d_post + b * P.sum_card,
+    launch_finalize(P.cpt_per_thread, pl->dp, A, nc, P.dcl[P.root].sep_row, d_lp + b, d_post + b * P.io_sum_card,
                     d_st + b, s);
   }
   cudaError_t e = cudaGetLastError();

@@ -287,6 +287,7 @@ extern "C" jt_status jt_server_create(int64_t arena_bytes, int32_t max_batch, in
 extern "C" jt_status jt_server_add_plan(jt_server *S, jt_plan *pl, int32_t *plan_id) {
   if (!S || !pl || !plan_id) { set_error("null argument"); return JT_EINVAL; }
   if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
+  if (pl->P.n_pruned > 0) { set_error("the server takes plans that are not pruned to a query set"); return JT_EINVAL; }
   std::lock_guard<std::mutex> lk(S->mu);
   if ((int64_t)slot_bytes(pl, S->max_batch, nullptr) > S->budget) {
     set_error("one batch of this plan does not fit the server's arena budget");

@@ -35,7 +35,7 @@ class CompileOpts(ctypes.Structure):
                 ("items_per_tile_distribute", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("wait_limit_us", ctypes.c_int32), ("stall_clique", ctypes.c_int32),
                 ("n_observed_set", ctypes.c_int32), ("observed_set", ctypes.c_void_p),
-                ("rescale", ctypes.c_int32)]
+                ("rescale", ctypes.c_int32), ("n_query_set", ctypes.c_int32), ("query_set", ctypes.c_void_p)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -48,7 +48,7 @@ class PlanInfo(ctypes.Structure):
                 ("collect_items", ctypes.c_int64), ("distribute_items", ctypes.c_int64),
                 ("algorithmic_bytes_per_case", ctypes.c_double),
                 ("kernels_per_chunk", ctypes.c_int32), ("sliced_vars", ctypes.c_int32),
-                ("separator_evidence_vars", ctypes.c_int32)]
+                ("separator_evidence_vars", ctypes.c_int32), ("pruned_vars", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,10 +115,12 @@ def _ptr(a):
 
 def default_opts(**kw) -> CompileOpts:
     """jt_compile_opts with the defaults, then the given fields.  observed_set
-    takes a sequence of variable ids (kept alive with the returned struct)."""
+    and query_set take sequences of variable ids (kept alive with the
+    returned struct)."""
     o = CompileOpts()
     lib.jt_default_opts(ctypes.byref(o))
     obs = kw.pop("observed_set", None)
+    qry = kw.pop("query_set", None)
     for k, v in kw.items():
         setattr(o, k, v)
     if obs is not None and len(obs) > 0:
@@ -126,6 +128,11 @@ def default_opts(**kw) -> CompileOpts:
         o._observed_keepalive = arr
         o.n_observed_set = int(arr.size)
         o.observed_set = arr.ctypes.data
+    if qry is not None and len(qry) > 0:
+        arr = np.ascontiguousarray(qry, dtype=np.int32)
+        o._query_keepalive = arr
+        o.n_query_set = int(arr.size)
+        o.query_set = arr.ctypes.data
     return o
 
 
@@ -151,8 +158,9 @@ def autotune(net, n_cases: int, **opts):
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
                                            "items_per_tile_distribute", "use_graphs", "arena_bytes",
                                            "max_clique_entries", "schedule", "rescale")}
-    if opts.get("observed_set") is not None:
-        out["observed_set"] = list(opts["observed_set"])
+    for k in ("observed_set", "query_set"):
+        if opts.get(k) is not None:
+            out[k] = list(opts[k])
     return out, ns.value
 
 

@@ -183,6 +183,7 @@ def test_observed_set_option():
     info = p.info()
     assert info["sliced_vars"] == len(obs)
     assert info["n_cliques"] == full["n_cliques"]
+    assert info["n_vars"] == net.n and info["sum_card"] == full["sum_card"] == int(np.sum(net.card))
     assert info["sum_clique_entries"] < full["sum_clique_entries"]
     size = lambda vs: int(np.prod([net.card[v] for v in vs])) if vs else 1
     total = 0
@@ -195,3 +196,42 @@ def test_observed_set_option():
         with pytest.raises(J.JTError) as e:
             _plan(net, observed_set=bad)
         assert e.value.status == J.JT_EINVAL
+
+
+def _ancestral_closure(net, roots):
+    keep, stack = set(), list(roots)
+    while stack:
+        v = stack.pop()
+        if v not in keep:
+            keep.add(v)
+            stack.extend(int(p) for p in net.parents_of(v))
+    return keep
+
+
+@pytest.mark.parametrize("name,q,o", [("bn60", [41, 50], [3, 17]), ("bn60", [59], []),
+                                      ("bn1000", [10, 500, 990], [20, 700]), ("bn110", [100], [5])])
+def test_query_set_pruning(name, q, o):
+    """A plan pruned to a query set keeps the query set, the observed set and
+    their ancestors (every other variable is barren); evidence and posterior
+    rows keep the full network's layout."""
+    net = configs.network(name)
+    p = _plan(net, query_set=q, observed_set=o)
+    info = p.info()
+    keep = _ancestral_closure(net, q + o)
+    assert info["pruned_vars"] == net.n - len(keep)
+    assert info["n_vars"] == net.n and info["sum_card"] == int(np.sum(net.card))
+    held = set()
+    for c in range(info["n_cliques"]):
+        held |= set(p.clique(c)[0])
+    assert held == keep - set(o)          # the observed set is also sliced out of the tables
+    for bad in ([3, 3], [net.n], [-2]):
+        with pytest.raises(J.JTError) as e:
+            _plan(net, query_set=bad)
+        assert e.value.status == J.JT_EINVAL
+
+
+def test_query_set_keeping_everything_is_the_full_plan():
+    net = configs.network("bn20")
+    sinks = [v for v in range(net.n) if all(v not in net.parents_of(u) for u in range(net.n))]
+    a, b = _plan(net, query_set=sinks).info(), _plan(net).info()
+    assert a["pruned_vars"] == 0 and a["sum_clique_entries"] == b["sum_clique_entries"]
