@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <mutex>
 #include <new>
@@ -683,7 +684,15 @@ extern "C" jt_status jt_infer_cpu(const jt_plan *pl, int32_t n_cases, const int3
   if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
   if (n_cases == 0) return JT_OK;
   if (!ev || !lp || !post || !cst) { set_error("null buffer"); return JT_EINVAL; }
-  return cpu_layers_infer(pl->P, n_cases, ev, lp, post, cst, n_threads);
+  try {
+    return cpu_layers_infer(pl->P, n_cases, ev, lp, post, cst, std::min<int32_t>(n_threads, 1024));
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed in the CPU comparator");
+    return JT_ENOMEM;
+  } catch (const std::exception &e) {
+    set_error(std::string("CPU comparator: ") + e.what());
+    return JT_EINVAL;
+  }
 }
 
 extern "C" jt_status jt_infer_plain(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp,

@@ -132,3 +132,23 @@ def test_pruned_plans_refused_by_other_paths():
     with pytest.raises(J.JTError) as e:
         srv.add_plan(p)
     assert e.value.status == J.JT_EINVAL
+
+
+def test_autotune_and_profile_on_pruned_plan():
+    net = configs.network("bn60")
+    q, obs = [41, 50], [3, 17]
+    opts, ns = J.autotune(net, 512, query_set=q, observed_set=obs)
+    assert opts["query_set"] == q and opts["observed_set"] == obs and ns > 0
+    plan = J.Plan(net, **opts)
+    keep = _closure(net, q + obs)
+    ev = _cases(net, 512, keep, obs, 0.1, seed=4)
+    _check(net, plan, ev, keep, "autotuned pruned plan")
+    d_ev = torch.from_numpy(ev).cuda()
+    d_lp = torch.empty(len(ev), dtype=torch.float64, device="cuda")
+    d_post = torch.empty((len(ev), plan.sum_card), dtype=torch.float64, device="cuda")
+    d_st = torch.empty(len(ev), dtype=torch.int32, device="cuda")
+    prof = plan.profile(d_ev, d_lp, d_post, d_st, stream=torch.cuda.current_stream().cuda_stream)
+    assert prof["collect_launches"] >= 1 and prof["total_ms"] > 0
+    lp, post, st = plan.infer(ev)
+    assert np.array_equal(st, d_st.cpu().numpy()) and np.array_equal(lp, d_lp.cpu().numpy())
+    assert np.array_equal(post, d_post.cpu().numpy(), equal_nan=True)

@@ -75,3 +75,24 @@ def test_noalloc_refuses_plan_larger_than_scratch():
     r = _noalloc(plan, d_ev, *out)
     assert r == J.JT_ENOMEM
     assert "static scratch" in J.lib.jt_last_error().decode()
+
+
+def test_noalloc_pruned_and_sliced_plan():
+    """Evidence and posterior rows of a pruned plan keep the full network's
+    layout on this entry point too."""
+    from synth.bn import sample_cases
+    net = configs.network("bn1000")
+    q, obs = [999, 400], [5, 600, 700]
+    x = sample_cases(net, 333, 1.0, seed=8)
+    ev = np.full_like(x, -1, dtype=np.int32)
+    ev[:, obs] = x[:, obs]
+    plan = J.Plan(net, query_set=q, observed_set=obs)
+    assert plan.info()["pruned_vars"] > 0
+    d_ev = torch.from_numpy(ev).cuda()
+    ref = _buffers(len(ev), plan.sum_card)
+    plan.infer_device(d_ev, *ref, stream=torch.cuda.current_stream().cuda_stream)
+    out = _buffers(len(ev), plan.sum_card)
+    assert _noalloc(plan, d_ev, *out) == J.JT_OK, J.lib.jt_last_error().decode()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, out):
+        assert np.array_equal(a.cpu().numpy(), b.cpu().numpy(), equal_nan=True)
