@@ -281,6 +281,7 @@ static jt_status upload_plan(jt_plan *pl) {
   const size_t o_dfp = put(blob, P.d_flow_pref), o_dfb = put(blob, P.d_flow_begin);
   const size_t o_cn = put(blob, P.c_need), o_cno = put(blob, P.c_notify), o_dn = put(blob, P.d_need);
   const size_t o_sv = put(blob, P.slice_var);
+  const size_t o_cvo = put(blob, P.comp_var_owner);
   const size_t o_iv = put(blob, P.io_var), o_id = put(blob, P.io_dropped);
   const size_t o_ipc = put(blob, P.io_post_col), o_inc = put(blob, P.io_nan_cols);
   JT_CUDA_TRY(cudaMalloc(&pl->d_static, blob.size()));
@@ -302,6 +303,8 @@ static jt_status upload_plan(jt_plan *pl) {
   D.comp_cliques = reinterpret_cast<const int32_t *>(b + o_cc);
   D.comp_roots = reinterpret_cast<const int32_t *>(b + o_cr);
   D.comp_owner = reinterpret_cast<const int32_t *>(b + o_co);
+  D.comp_var_owner = reinterpret_cast<const int32_t *>(b + o_cvo);
+  D.n_comp_vars = (int32_t)P.comp_vars.size();
   D.n_comp_cliques = (int32_t)P.comp_cliques.size();
   D.n_comp = (int32_t)P.comp_roots.size();
   D.pgroup_ptr = reinterpret_cast<const int32_t *>(b + o_pg);

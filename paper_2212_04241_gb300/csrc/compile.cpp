@@ -926,6 +926,12 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       const DClique &D = P.dcl[P.comp_roots[q]];
       for (int k = D.comp_begin; k < D.comp_end; ++k) P.comp_owner[k] = (int32_t)q;
     }
+    // component of each comp_vars entry (only component roots list variables)
+    P.comp_var_owner.assign(P.comp_vars.size(), 0);
+    for (size_t q = 0; q < P.comp_roots.size(); ++q) {
+      const int cl = P.comp_roots[q];
+      for (int k = P.comp_ptr[cl]; k < P.comp_ptr[cl + 1]; ++k) P.comp_var_owner[k] = (int32_t)q;
+    }
   }
 
   // ---------------------------------------------------------------------

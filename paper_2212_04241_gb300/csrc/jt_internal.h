@@ -174,6 +174,7 @@ struct Plan {
   std::vector<int32_t> comp_cliques;  // non-root cliques of each component, grouped by component
   std::vector<int32_t> comp_roots;    // component root cliques
   std::vector<int32_t> comp_owner;    // per comp_cliques entry: its component (index into comp_roots)
+  std::vector<int32_t> comp_var_owner;  // per comp_vars entry: its component (index into comp_roots)
   std::vector<int32_t> pgroup_ptr;    // consecutive variable groups of <= 16 posterior columns
   // dataflow schedule (see DevPlan)
   std::vector<int64_t> c_flow_pref, c_flow_begin, d_flow_pref, d_flow_begin;

@@ -761,14 +761,13 @@ __global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *_
   for (int q = slice * 32 + c; q < P.n_comp; q += 32 * kLogpeSlices) s_obs[q] = 0u;
   __syncthreads();
   // phase 1: components with an observed variable (a component without one
-  // has probability exactly 1: a sum over all states of a product of CPTs)
-  for (int q = slice; q < P.n_comp; q += kLogpeSlices) {
-    const int cl = P.comp_roots[q];
-    bool observed = false;
-    for (int k = P.comp_ptr[cl]; k < P.comp_ptr[cl + 1] && !observed; ++k)
-      observed = A.ev[((int64_t)tile * P.n_vars + P.comp_vars[k]) * W + col] >= 0;
-    if (observed) atomicOr(&s_obs[q], 1u << c);
-  }
+  // has probability exactly 1: a sum over all states of a product of CPTs);
+  // the (component, variable) pairs are spread over the slices
+  for (int k = slice; k < P.n_comp_vars; k += kLogpeSlices)
+    if (A.ev[((int64_t)tile * P.n_vars + P.comp_vars[k]) * W + col] >= 0) {
+      const int q = P.comp_var_owner[k];
+      if (!((s_obs[q] >> c) & 1u)) atomicOr(&s_obs[q], 1u << c);
+    }
   __syncthreads();
   // phase 2: messages multiplied into a parent were scaled by 2^-k, so k is
   // added back; every observed component root adds the log of its total

@@ -25,6 +25,8 @@ struct DevPlan {
   const int32_t *comp_cliques;  // non-root cliques of each component
   const int32_t *comp_roots;    // [n_comp] component root cliques
   const int32_t *comp_owner;    // per comp_cliques entry: its component
+  const int32_t *comp_var_owner;  // per comp_vars entry: its component
+  int32_t n_comp_vars;          // entries of comp_vars
   int32_t n_comp_cliques;       // entries of comp_cliques
   const int32_t *pgroup_ptr;    // [n_pgroups + 1] variable groups of the posterior kernel
   // dataflow schedule: per pass, the items of each flow layer (collect:
