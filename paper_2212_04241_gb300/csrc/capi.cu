@@ -350,6 +350,7 @@ static jt_status upload_plan(jt_plan *pl) {
     return JT_ETOOBIG;
   }
   JT_CUDA_TRY(configure_logpe_smem((int)P.comp_roots.size()));
+  JT_CUDA_TRY(configure_posterior_smem());
   int sms = 0;
   JT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
   pl->flow_collect_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, true, P.n_sliced > 0, max_maps);

@@ -809,7 +809,7 @@ __global__ void k_logpe(DevPlan P, DevArena A, int W, int32_t n_cases, double *_
 
 __global__ void k_posterior(DevPlan P, DevArena A, int W, int32_t n_cases, const int32_t *__restrict__ status,
                             double *__restrict__ post) {
-  extern __shared__ double stage[];  // [W][kStageCols + 1]
+  extern __shared__ double stage[];  // [W][kStageCols + 1], then float [kStageCols][W] inputs
   const int tile = blockIdx.x;
   const int c = threadIdx.x;
   const int64_t cs = (int64_t)tile * W + c;
@@ -834,7 +834,43 @@ __global__ void k_posterior(DevPlan P, DevArena A, int W, int32_t n_cases, const
             stage[rr * (kStageCols + 1) + j];
     __syncthreads();
   };
-  for (int v = v0; v < v1; ++v) {
+  const int ncols_all = (int)(P.post_off[v1 - 1] + P.card[v1 - 1] - col0);
+  if (ncols_all <= kStageCols) {
+    // every input of the group requested at once (one load each, no chain
+    // of dependent loads), then normalised from shared memory; each thread
+    // touches only its own case's column of `in`
+    float *in = reinterpret_cast<float *>(stage + (size_t)W * (kStageCols + 1));
+    const float *m0 = A.post + ((int64_t)tile * P.post_rows + col0) * W + c;
+    float x[kStageCols];
+    int e[kStageCols];
+#pragma unroll
+    for (int j = 0; j < kStageCols; ++j) x[j] = j < ncols_all ? m0[(int64_t)j * W] : 0.f;
+#pragma unroll
+    for (int k = 0; k < kStageCols; ++k) e[k] = v0 + k < v1 ? A.ev[((int64_t)tile * P.n_vars + v0 + k) * W + c] : -1;
+#pragma unroll
+    for (int j = 0; j < kStageCols; ++j) in[j * W + c] = x[j];
+#pragma unroll
+    for (int k = 0; k < kStageCols; ++k) {
+      if (v0 + k < v1) {  // the same for every thread of the block
+        const int o = (int)(P.post_off[v0 + k] - col0);
+        const int r = P.card[v0 + k];
+        double s = 0.0;
+        if (st == JT_CASE_OK && e[k] < 0)
+          for (int j = 0; j < r; ++j) s += (double)in[(o + j) * W + c];
+        const double inv = 1.0 / s;
+        for (int j = 0; j < r; ++j) {
+          double val;
+          if (st != JT_CASE_OK) val = NAN;
+          else if (e[k] >= 0) val = (j == e[k]) ? 1.0 : 0.0;
+          else val = (double)in[(o + j) * W + c] * inv;
+          stage[c * (kStageCols + 1) + o + j] = val;
+        }
+      }
+    }
+    flush(ncols_all);
+    return;
+  }
+  for (int v = v0; v < v1; ++v) {  // a variable with more than kStageCols states
     const int64_t off = P.post_off[v];
     const int r = P.card[v];
     const int ev = A.ev[((int64_t)tile * P.n_vars + v) * W + c];
@@ -1072,6 +1108,15 @@ cudaError_t configure_logpe_smem(int n_comp) {
   return cudaFuncSetAttribute(k_logpe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+size_t posterior_smem_bytes(int W) {
+  return sizeof(double) * (size_t)W * (kStageCols + 1) + sizeof(float) * (size_t)kStageCols * W;
+}
+
+cudaError_t configure_posterior_smem() {
+  return cudaFuncSetAttribute(k_posterior, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)posterior_smem_bytes(32 * 8));
+}
+
 void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cases,
                      int64_t root_sep_row, double *d_log_pe, double *d_post, int32_t *d_status,
                      cudaStream_t s) {
@@ -1081,7 +1126,7 @@ void launch_finalize(int cpt, const DevPlan &P, const DevArena &A, int32_t n_cas
   const unsigned tiles = (unsigned)((n_cases + W - 1) / W);
   const size_t lsmem = logpe_smem_bytes(P.n_comp);
   k_logpe<<<(unsigned)((n_cases + 31) / 32), dim3(32, kLogpeSlices), lsmem, s>>>(P, A, W, n_cases, d_log_pe, d_status);
-  const size_t smem = sizeof(double) * (size_t)W * (kStageCols + 1);
+  const size_t smem = posterior_smem_bytes(W);
   k_posterior<<<dim3(tiles, (unsigned)(P.n_pgroups + (P.n_nan_cols > 0))), W, smem, s>>>(P, A, W, n_cases,
                                                                                          d_status, d_post);
 }

@@ -102,6 +102,9 @@ cudaError_t configure_collect_smem(int cpt, bool sliced, size_t bytes);
 // the log P(e) kernel keeps one word per component tree in shared memory
 size_t logpe_smem_bytes(int n_comp);
 cudaError_t configure_logpe_smem(int n_comp);
+// the posterior kernel stages a case tile's outputs and inputs in shared memory
+size_t posterior_smem_bytes(int W);
+cudaError_t configure_posterior_smem();
 constexpr int kMaxTilesPerChunk = 16384;
 // dataflow schedule: one persistent launch per pass (blocks = SMs x resident blocks per SM)
 void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s);
