@@ -500,7 +500,7 @@ static cudaStream_t pick_stream(jt_plan *pl, void *s) {
   return s ? static_cast<cudaStream_t>(s) : pl->stream;
 }
 
-extern "C" jt_status jt_infer_device(jt_plan *pl, int32_t n_cases, const int32_t *d_ev, double *d_lp,
+static jt_status jt_infer_device_impl(jt_plan *pl, int32_t n_cases, const int32_t *d_ev, double *d_lp,
                                      double *d_post, int32_t *d_st, void *stream) {
   if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
   if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
@@ -521,6 +521,11 @@ extern "C" jt_status jt_infer_device(jt_plan *pl, int32_t n_cases, const int32_t
   return JT_OK;
 }
 
+extern "C" jt_status jt_infer_device(jt_plan *pl, int32_t n_cases, const int32_t *d_ev, double *d_lp,
+                                     double *d_post, int32_t *d_st, void *stream) {
+  return guarded([&] { return jt_infer_device_impl(pl, n_cases, d_ev, d_lp, d_post, d_st, stream); });
+}
+
 static jt_status ensure_io(jt_plan *pl, int cases) {
   if (pl->io_cases >= cases) return JT_OK;
   free_io(pl);
@@ -536,7 +541,7 @@ static jt_status ensure_io(jt_plan *pl, int cases) {
   return JT_OK;
 }
 
-extern "C" jt_status jt_infer(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp, double *post,
+static jt_status jt_infer_impl(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp, double *post,
                               int32_t *cst, void *stream) {
   if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
   if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
@@ -601,6 +606,11 @@ extern "C" jt_status jt_infer(jt_plan *pl, int32_t n_cases, const int32_t *ev, d
     std::memcpy(cst + b, h_st, sizeof(int32_t) * nc);
   }
   return JT_OK;
+}
+
+extern "C" jt_status jt_infer(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp, double *post,
+                              int32_t *cst, void *stream) {
+  return guarded([&] { return jt_infer_impl(pl, n_cases, ev, lp, post, cst, stream); });
 }
 
 // ---------------------------------------------------------------------------
@@ -699,7 +709,7 @@ extern "C" jt_status jt_infer_cpu(const jt_plan *pl, int32_t n_cases, const int3
   }
 }
 
-extern "C" jt_status jt_infer_plain(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp,
+static jt_status jt_infer_plain_impl(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp,
                                     double *post, int32_t *cst, void *stream) {
   if (!pl || n_cases < 0) { set_error("bad plan or n_cases"); return JT_EINVAL; }
   if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
@@ -756,10 +766,15 @@ extern "C" jt_status jt_infer_plain(jt_plan *pl, int32_t n_cases, const int32_t 
   return JT_OK;
 }
 
+extern "C" jt_status jt_infer_plain(jt_plan *pl, int32_t n_cases, const int32_t *ev, double *lp,
+                                    double *post, int32_t *cst, void *stream) {
+  return guarded([&] { return jt_infer_plain_impl(pl, n_cases, ev, lp, post, cst, stream); });
+}
+
 // ---------------------------------------------------------------------------
 // instrumented run (per-kernel timing with CUDA events)
 // ---------------------------------------------------------------------------
-extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_ev, double *d_lp,
+static jt_status jt_profile_impl(jt_plan *pl, int32_t n_cases, const int32_t *d_ev, double *d_lp,
                                 double *d_post, int32_t *d_st, void *stream, double *out) {
   if (!pl || n_cases <= 0 || !out) { set_error("bad argument"); return JT_EINVAL; }
   if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
@@ -845,10 +860,15 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
   return JT_OK;
 }
 
+extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_ev, double *d_lp,
+                                double *d_post, int32_t *d_st, void *stream, double *out) {
+  return guarded([&] { return jt_profile_impl(pl, n_cases, d_ev, d_lp, d_post, d_st, stream, out); });
+}
+
 // ---------------------------------------------------------------------------
 // autotuner: time candidate tile shapes on the caller's batch size
 // ---------------------------------------------------------------------------
-extern "C" jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
+static jt_status jt_autotune_impl(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
                                  const int32_t *parents, const double *cpt, const jt_compile_opts *base,
                                  int32_t n_cases, jt_compile_opts *best, double *best_ns_per_case) {
   if (!best || n_cases <= 0 || n_vars <= 0 || !card) { set_error("bad argument"); return JT_EINVAL; }
@@ -921,4 +941,12 @@ extern "C" jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int3
   *best = best_o;
   if (best_ns_per_case) *best_ns_per_case = best_total * 1e6 / n_cases;
   return JT_OK;
+}
+
+extern "C" jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
+                                 const int32_t *parents, const double *cpt, const jt_compile_opts *base,
+                                 int32_t n_cases, jt_compile_opts *best, double *best_ns_per_case) {
+  return guarded([&] {
+    return jt_autotune_impl(n_vars, card, parent_ptr, parents, cpt, base, n_cases, best, best_ns_per_case);
+  });
 }

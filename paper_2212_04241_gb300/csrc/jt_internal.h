@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -216,6 +218,21 @@ jt_status build_plan_pruned(int32_t n, const int32_t *card, const int32_t *pptr,
                             const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err);
 
 void set_error(const std::string &msg);
+
+// Runs the body of a C entry point: a C++ exception (a failed host
+// allocation, a thread that cannot start) becomes a status, never an abort.
+template <class F>
+jt_status guarded(F &&body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed");
+    return JT_ENOMEM;
+  } catch (const std::exception &e) {
+    set_error(std::string("host error: ") + e.what());
+    return JT_EINVAL;
+  }
+}
 
 // cpu_layers.cpp: the multi-core CPU comparator (jt_infer_cpu)
 jt_status cpu_layers_infer(const Plan &P, int32_t n_cases, const int32_t *ev, double *log_pe, double *post,

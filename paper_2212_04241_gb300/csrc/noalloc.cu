@@ -50,7 +50,7 @@ jt_status scratch_for(int device, void **out) {
 
 }  // namespace
 
-extern "C" jt_status jt_infer_device_noalloc(jt_plan *pl, int32_t n_cases, const int32_t *d_ev,
+static jt_status jt_infer_device_noalloc_impl(jt_plan *pl, int32_t n_cases, const int32_t *d_ev,
                                              double *d_lp, double *d_post, int32_t *d_st,
                                              void *stream) {
   using namespace jt;
@@ -106,4 +106,10 @@ extern "C" jt_status jt_infer_device_noalloc(jt_plan *pl, int32_t n_cases, const
     return JT_ECUDA;
   }
   return JT_OK;
+}
+
+extern "C" jt_status jt_infer_device_noalloc(jt_plan *pl, int32_t n_cases, const int32_t *d_ev,
+                                             double *d_lp, double *d_post, int32_t *d_st,
+                                             void *stream) {
+  return jt::guarded([&] { return jt_infer_device_noalloc_impl(pl, n_cases, d_ev, d_lp, d_post, d_st, stream); });
 }

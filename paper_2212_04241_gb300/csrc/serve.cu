@@ -269,7 +269,8 @@ extern "C" jt_status jt_server_create(int64_t arena_bytes, int32_t max_batch, in
   if (!out) { set_error("out is NULL"); return JT_EINVAL; }
   *out = nullptr;
   if (max_batch <= 0 || max_inflight <= 0) { set_error("max_batch and max_inflight must be > 0"); return JT_EINVAL; }
-  jt_server *S = new jt_server();
+  jt_server *S = new (std::nothrow) jt_server();
+  if (!S) { set_error("host allocation failed"); return JT_ENOMEM; }
   S->budget = arena_bytes > 0 ? arena_bytes : (16LL << 30);
   S->max_batch = max_batch;
   S->max_inflight = max_inflight;
@@ -279,12 +280,18 @@ extern "C" jt_status jt_server_create(int64_t arena_bytes, int32_t max_batch, in
     set_error("no CUDA device");
     return JT_ECUDA;
   }
-  S->worker = std::thread(worker_main, S);
+  try {
+    S->worker = std::thread(worker_main, S);
+  } catch (const std::exception &e) {
+    delete S;
+    set_error(std::string("server thread: ") + e.what());
+    return JT_EINVAL;
+  }
   *out = S;
   return JT_OK;
 }
 
-extern "C" jt_status jt_server_add_plan(jt_server *S, jt_plan *pl, int32_t *plan_id) {
+static jt_status jt_server_add_plan_impl(jt_server *S, jt_plan *pl, int32_t *plan_id) {
   if (!S || !pl || !plan_id) { set_error("null argument"); return JT_EINVAL; }
   if (pl->host_only) { set_error("plan compiled with host_only"); return JT_EINVAL; }
   if (pl->P.n_pruned > 0) { set_error("the server takes plans that are not pruned to a query set"); return JT_EINVAL; }
@@ -298,7 +305,11 @@ extern "C" jt_status jt_server_add_plan(jt_server *S, jt_plan *pl, int32_t *plan
   return JT_OK;
 }
 
-extern "C" jt_status jt_submit(jt_server *S, int32_t plan_id, const int32_t *ev, const int32_t *query,
+extern "C" jt_status jt_server_add_plan(jt_server *S, jt_plan *pl, int32_t *plan_id) {
+  return guarded([&] { return jt_server_add_plan_impl(S, pl, plan_id); });
+}
+
+static jt_status jt_submit_impl(jt_server *S, int32_t plan_id, const int32_t *ev, const int32_t *query,
                                int32_t n_query, uint64_t *ticket) {
   if (!S || !ev || !ticket) { set_error("null argument"); return JT_EINVAL; }
   Request r;
@@ -323,7 +334,12 @@ extern "C" jt_status jt_submit(jt_server *S, int32_t plan_id, const int32_t *ev,
   return JT_OK;
 }
 
-extern "C" jt_status jt_poll(jt_server *S, uint64_t ticket, double *log_pe, double *post, int32_t *cst) {
+extern "C" jt_status jt_submit(jt_server *S, int32_t plan_id, const int32_t *ev, const int32_t *query,
+                               int32_t n_query, uint64_t *ticket) {
+  return guarded([&] { return jt_submit_impl(S, plan_id, ev, query, n_query, ticket); });
+}
+
+static jt_status jt_poll_impl(jt_server *S, uint64_t ticket, double *log_pe, double *post, int32_t *cst) {
   if (!S) { set_error("null server"); return JT_EINVAL; }
   std::lock_guard<std::mutex> lk(S->mu);
   auto it = S->results.find(ticket);
@@ -351,6 +367,10 @@ extern "C" jt_status jt_poll(jt_server *S, uint64_t ticket, double *log_pe, doub
   return JT_OK;
 }
 
+extern "C" jt_status jt_poll(jt_server *S, uint64_t ticket, double *log_pe, double *post, int32_t *cst) {
+  return guarded([&] { return jt_poll_impl(S, ticket, log_pe, post, cst); });
+}
+
 extern "C" jt_status jt_server_drain(jt_server *S) {
   if (!S) { set_error("null server"); return JT_EINVAL; }
   std::unique_lock<std::mutex> lk(S->mu);
@@ -359,7 +379,7 @@ extern "C" jt_status jt_server_drain(jt_server *S) {
   return JT_OK;
 }
 
-extern "C" jt_status jt_server_stats(jt_server *S, int64_t *out) {
+static jt_status jt_server_stats_impl(jt_server *S, int64_t *out) {
   if (!S || !out) { set_error("null argument"); return JT_EINVAL; }
   std::lock_guard<std::mutex> lk(S->mu);
   out[0] = S->completed;
@@ -380,6 +400,10 @@ extern "C" jt_status jt_server_stats(jt_server *S, int64_t *out) {
   }
   out[6] = S->pending + S->inflight;
   return JT_OK;
+}
+
+extern "C" jt_status jt_server_stats(jt_server *S, int64_t *out) {
+  return guarded([&] { return jt_server_stats_impl(S, out); });
 }
 
 extern "C" void jt_server_destroy(jt_server *S) {
