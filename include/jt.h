@@ -18,6 +18,13 @@
  * order and lets each case tile advance as soon as its own producers are
  * done; JT_SCHEDULE_LAYERS runs one launch per layer instead.
  *
+ * Plans can be specialised at compile time: to an observed set that every
+ * case observes (its dimensions sliced out of the tables) and to a query
+ * set (barren variables removed); see jt_compile_opts.  Two comparators sit
+ * beside the batched path for measurement: jt_infer_plain (per-case FP64
+ * on the GPU, element-wise style) and jt_infer_cpu (the paper's own
+ * layer-parallel design on the host cores).
+ *
  * Conventions shared by every call:
  *   - Variables are numbered 0..n-1.  card[v] >= 2 is the number of states.
  *   - Parents are given in CSR form: the parents of v are
@@ -30,7 +37,8 @@
  *   - Evidence is int32 [n_cases][n]: the observed state of v, or -1.
  *   - Outputs: log_pe float64 [n_cases] (natural log of P(e));
  *     posteriors float64 [n_cases][sum(card)], the states of v at offsets
- *     sum(card[0..v-1]) ...; an observed variable gets a point mass;
+ *     sum(card[0..v-1]) ...; an observed variable gets a point mass (and a
+ *     variable removed from a plan pruned to a query set gets NaN);
  *     case_status int32 [n_cases] (JT_CASE_*).
  *   - Every call returns a jt_status and never aborts.  The caller owns all
  *     buffers it passes; inputs are read during the call only.
