@@ -574,6 +574,15 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
 #pragma unroll
       for (int g = 0; g < G; ++g)
         p[g] = ldrow<CPT, LD_STREAM>(psi + (int64_t)__shfl_sync(kFull, ej, min(r + g, nb - 1)) * W, lane);
+      // the next group's rows are requested into L2 now: more bytes in
+      // flight at the register-limited occupancy, without holding registers
+      if (r + G < nb) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const float *pa = psi + (int64_t)__shfl_sync(kFull, ej, min(r + G + g, nb - 1)) * W + lane * CPT;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+        }
+      }
       if (!root) {
         Vec<CPT> q[G];
 #pragma unroll
