@@ -95,9 +95,13 @@ jt_status arena_alloc(const Plan &P, Arena &a, int tiles) {
   }
   a.owns = true;
   arena_bind(P, a, static_cast<char *>(mem), tiles);
-  // counters start at zero; every combining warp resets its own counter
+  // counters start at zero; every combining warp resets its own counter.
+  // cudaMemset runs on the legacy default stream, which does not order the
+  // library's non-blocking streams: wait for it before any batch can use
+  // the arena (fresh memory may hold another arena's old data)
   JT_CUDA_TRY(cudaMemset(a.da.counters, 0, L.counters * (size_t)tiles));
   JT_CUDA_TRY(cudaMemset(a.da.errflag, 0, sizeof(uint32_t)));
+  JT_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
   return JT_OK;
 }
 
@@ -200,6 +204,7 @@ jt_status check_arena_flag(Arena &a) {
   JT_CUDA_TRY(cudaMemcpy(&f, a.da.errflag, sizeof(f), cudaMemcpyDeviceToHost));
   if (f) {
     cudaMemset(a.da.errflag, 0, sizeof(uint32_t));
+    cudaStreamSynchronize(cudaStreamLegacy);  // cleared before the next batch is issued
     set_error("a bounded device wait for work on the same case tile expired");
     return JT_ETIMEOUT;
   }
@@ -287,6 +292,9 @@ static jt_status upload_plan(jt_plan *pl) {
   JT_CUDA_TRY(cudaMalloc(&pl->d_static, blob.size()));
   pl->static_bytes = blob.size();
   JT_CUDA_TRY(cudaMemcpy(pl->d_static, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  // a host-to-device cudaMemcpy may return before its last bytes land, and
+  // the legacy stream does not order the plan's non-blocking streams
+  JT_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
   char *b = static_cast<char *>(pl->d_static);
   DevPlan &D = pl->dp;
   D.cl = reinterpret_cast<const DClique *>(b + o_cl);
@@ -639,6 +647,7 @@ static jt_status ensure_plain(jt_plan *pl) {
     return JT_ENOMEM;
   }
   JT_CUDA_TRY(cudaMemcpy(mem, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  JT_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));  // see upload_plan
   char *b = static_cast<char *>(mem);
   pl->d_plain = mem;
   pl->pw.base = reinterpret_cast<double *>(b + o_b);
@@ -893,6 +902,7 @@ static jt_status jt_autotune_impl(int32_t n_vars, const int32_t *card, const int
   }
   // all variables unobserved: the timing does not depend on the evidence values
   cudaMemset(d_ev, 0xff, sizeof(int32_t) * (size_t)n_cases * n_vars);
+  cudaStreamSynchronize(cudaStreamLegacy);  // filled before the plans' streams read it
   jt_status result = JT_OK;
   double best_total = -1;
   jt_compile_opts best_o = b;
