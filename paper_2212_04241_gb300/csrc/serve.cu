@@ -139,6 +139,9 @@ bool slot_launch(jt_server *S, Slot &s, std::vector<Request> &&reqs) {
   int32_t *h_ev = reinterpret_cast<int32_t *>(h);
   for (int i = 0; i < nb; ++i) std::memcpy(h_ev + (size_t)i * P.n, reqs[i].ev.data(), sizeof(int32_t) * P.n);
   cudaMemcpyAsync(d, h, sizeof(int32_t) * (size_t)nb * P.n, cudaMemcpyHostToDevice, s.stream);
+  // a batch that hit an expired device wait left the slot's flag set (its
+  // cases reported JT_CASE_INCOMPLETE); the slot is idle, so clear it
+  cudaMemsetAsync(s.arena.da.errflag, 0, sizeof(uint32_t), s.stream);
   jt_status st;
   {
     std::lock_guard<std::mutex> lk(pl->mu);
