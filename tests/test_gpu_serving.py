@@ -156,3 +156,30 @@ def test_admission_by_arena_bytes(plans):
     st = srv.stats()
     assert st["peak_arena_bytes"] <= budget
     srv.close()
+
+
+def test_expired_device_wait_in_a_served_batch():
+    """A plan whose dataflow waits expire (the testing option stall_clique
+    makes one clique wait for a producer that does not exist, limit 2 ms):
+    its requests come back as JT_CASE_INCOMPLETE with NaN outputs, batch
+    after batch, while another plan served alongside stays correct."""
+    net = configs.network("bn60")
+    good = J.Plan(net, cases_per_thread=1)
+    bad = J.Plan(net, cases_per_thread=1, stall_clique=good.info()["root"] + 1, wait_limit_us=2000)
+    ev = configs.evidence("bn60", net, n_cases=6, seed=21)
+    srv = J.Server(arena_bytes=4 << 30, max_batch=8, max_inflight=4)
+    pg, pb = srv.add_plan(good), srv.add_plan(bad)
+    for _ in range(2):                        # two rounds: the slot serves again after a failure
+        tb = [srv.submit(pb, e) for e in ev[:3]]
+        tg = [srv.submit(pg, e) for e in ev[3:]]
+        out_len = {t: good.sum_card for t in tb + tg}
+        res = _wait(srv, tb + tg, out_len)
+        for t in tb:
+            lp, post, st = res[t]
+            assert st == J.JT_CASE_INCOMPLETE and np.isnan(lp)
+        olp, opost, ost = oracle.Oracle(net).infer(ev[3:])
+        lp = np.array([res[t][0] for t in tg])
+        post = np.stack([res[t][1] for t in tg])
+        st = np.array([res[t][2] for t in tg], dtype=np.int32)
+        assert_parity32(lp, post, st, olp, opost, ost, where="served beside a stalled plan")
+    srv.close()
