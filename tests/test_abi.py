@@ -43,3 +43,32 @@ def test_host_only_plan_refuses_inference():
         raise AssertionError("expected an error")
     except J.JTError as e:
         assert e.status == J.JT_EINVAL
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of jt_compile_opts and jt_plan_info_t have the
+    header's field offsets and sizes (a C program compiled against
+    include/jt.h prints them)."""
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "jt.h"', "int main(void) {"]
+    for cname, py in (("jt_compile_opts", J.CompileOpts), ("jt_plan_info_t", J.PlanInfo)):
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in (("jt_compile_opts", J.CompileOpts), ("jt_plan_info_t", J.PlanInfo)):
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
