@@ -65,3 +65,45 @@ def test_invalid_evidence_and_refusals():
     with pytest.raises(J.JTError) as e:
         J.Plan(net, host_only=1, observed_set=[1, 2]).infer_cpu(ev[:1])
     assert e.value.status == J.JT_EINVAL
+
+
+def test_drawn_networks_against_enumeration():
+    """Hypothesis-drawn tiny networks and evidence (impossible evidence
+    included): the comparator equals brute-force enumeration of the joint,
+    with 1 and 3 threads."""
+    hypothesis = pytest.importorskip("hypothesis")
+    from hypothesis import given, settings, HealthCheck, strategies as st
+    from synth.bn import make_network
+    from tests.refsolvers import brute_force, joint
+
+    @st.composite
+    def cases(draw):
+        n = draw(st.integers(1, 8))
+        card = [draw(st.integers(2, 3)) for _ in range(n)]
+        parents = []
+        for v in range(n):
+            k = draw(st.integers(0, min(v, 3)))
+            parents.append(sorted(draw(st.lists(st.integers(0, v - 1), min_size=k, max_size=k, unique=True)))
+                           if v else [])
+        net = make_network(n, card, parents, draw(st.sampled_from([0.3, 1.0])),
+                           np.random.default_rng(draw(st.integers(0, 2 ** 31 - 1))))
+        rows = draw(st.lists(st.lists(st.integers(-1, 2), min_size=n, max_size=n), min_size=1, max_size=4))
+        ev = np.array([[min(x, card[v] - 1) for v, x in enumerate(r)] for r in rows], dtype=np.int32)
+        return net, ev
+
+    @settings(max_examples=150, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+    @given(cases())
+    def check(case):
+        net, ev = case
+        blp, bpost = brute_force(net, ev, joint(net))
+        zero = ~np.isfinite(blp)
+        p = J.Plan(net, host_only=1)
+        for t in (1, 3):
+            lp, post, st_ = p.infer_cpu(ev, threads=t)
+            assert np.array_equal(st_ == J.JT_CASE_ZERO_EVIDENCE, zero)
+            ok = ~zero
+            if ok.any():
+                np.testing.assert_allclose(lp[ok], blp[ok], rtol=0, atol=TOL64 * max(1.0, np.abs(blp[ok]).max()))
+                np.testing.assert_allclose(post[ok], bpost[ok], rtol=0, atol=TOL64)
+
+    check()
