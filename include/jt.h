@@ -42,6 +42,15 @@
  *     case_status int32 [n_cases] (JT_CASE_*).
  *   - Every call returns a jt_status and never aborts.  The caller owns all
  *     buffers it passes; inputs are read during the call only.
+ *   - Concurrency: calls on different plans are independent.  Calls on one
+ *     plan from several host threads are serialised by the plan, but its
+ *     batched calls share one set of per-batch device tables, so their
+ *     device work must also be ordered: issue them on one stream (or order
+ *     the streams) -- jt_infer and jt_profile synchronise before returning,
+ *     jt_infer_device does not.  jt_infer_cpu only reads the plan.
+ *     jt_plan_free must not overlap any call on the plan.  A server keeps
+ *     its own per-batch tables for each batch in flight and serialises its
+ *     calls internally.
  *   - Accuracy of the FP32 batched path against exact FP64 arithmetic:
  *     max abs posterior error <= 1e-5 and |d log P(e)| <= 1e-6*max(1,|log P(e)|)
  *     on the workloads this library is tested on.
