@@ -3,9 +3,11 @@
 
 One step = one full inference pass (evidence reduction, collect, distribute,
 log P(e) and posterior normalisation for every case) over one batch of the
-workload's evidence cases.  Default workload: the 60-variable network
-(cardinality 2..5, largest clique <= 1e5 entries) with 4096 cases and 10 %
-observed, synthetic and seeded (synth/).
+workload's evidence cases.  Default workload: the 420-variable large-clique
+network (cardinality 2..4, 1-4 parents from the previous 14, largest clique
+between 4e6 and 1.6e7 entries), 5 % observed, with the batch set to the
+largest number of cases one table arena admits under the memory budget;
+synthetic and seeded (synth/).
 
 Reported on one JSON line (rank 0):
   value       device-resident throughput (evidence already in HBM), cases/s
@@ -45,19 +47,20 @@ WORKLOADS = {
     "bn420": "bn420_card2-4_Barena_obs5pct",
     "bn1000": "bn1000_ternary_B4096_obs5-30pct",
 }
-DEFAULT_CASES = {"bn20": 100, "bn60": 4096, "bn110": 8192, "bn420": 1024, "bn1000": 4096}
+# cases per step; None = the largest batch one table arena admits under the
+# plan's memory budget (the workload's batch is set by admission)
+DEFAULT_CASES = {"bn20": 100, "bn60": 4096, "bn110": 8192, "bn420": None, "bn1000": 4096}
+
+# the benchmark's metric, printed identically by both arms
+METRIC = "evidence cases/sec at \u22641e-5 posterior error, batched vs plain; p50/p99 latency"
 
 
 # DRAM traffic of the dominant kernel per launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the full-size workload,
-# profiles/dram_traffic_dataflow_bn60_B4096.md), valid only for the plan
-# shape and kernel source it was taken with: keyed by (workload, cases,
-# items_per_tile_distribute, sha256 prefix of csrc/kernels.cu); anything
-# else reports null.
-MEASURED_TRAFFIC = {
-    ("bn60", 4096, 192, "7e7d4a9a107b92ef"): 2093781248,
-    ("bn60", 4096, 384, "7e7d4a9a107b92ef"): 2010792448,
-}
+# dram__bytes_write.sum from one ncu capture), valid only for the plan shape
+# and kernel source it was taken with: keyed by (workload, cases, a key of
+# the plan's distribute work shape, sha256 prefix of csrc/kernels.cu);
+# anything else reports null.
+MEASURED_TRAFFIC = {}
 
 
 def _kept_columns(net, roots):
@@ -281,10 +284,14 @@ def run_reference(args, name, net, ev, rank, world):
     if rank != 0:
         return 0
     cores = os.cpu_count() or 1
-    # one step = a bounded sample of the workload on all host cores
-    per_step = min(ev.shape[0], max(cores * 8, 64))
     import oracle
     o = oracle.Oracle(net)
+    # one step = a bounded sample of the workload on all host cores: one case
+    # per core, or more while a step stays near a second
+    t0 = time.perf_counter()
+    o.infer(ev[:cores], threads=cores)
+    t_one = max(time.perf_counter() - t0, 1e-6)
+    per_step = int(min(ev.shape[0], cores * max(1, min(8, int(1.0 / t_one)))))
     for i in range(args.warmup):
         o.infer(ev[:per_step], threads=cores)
     times = []
@@ -295,7 +302,7 @@ def run_reference(args, name, net, ev, rank, world):
         times.append(time.perf_counter() - t0)
     total = float(np.sum(times))
     value = per_step * args.steps / total
-    line = {"metric": "evidence cases/sec at <=1e-5 posterior error", "value": value,
+    line = {"metric": METRIC, "value": value,
             "unit": "cases/s", "impl": "reference", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -315,7 +322,7 @@ def main():
                     help="timed steps; default: as many as fill about 2 s")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bn60", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="bn420", choices=sorted(WORKLOADS))
     ap.add_argument("--cases", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -342,18 +349,12 @@ def main():
     from synth import configs
     name = args.workload
     net = configs.network(name)
-    n_cases = args.cases or DEFAULT_CASES[name]
-    # every rank gets its own independent batch (weak scaling)
-    ev = configs.evidence(name, net, n_cases=n_cases, seed=rank_evidence_seed(name, rank))
+    arena_sized = not args.cases and DEFAULT_CASES[name] is None
     observed_set = None
     if args.observed_set > 0:
         # a fixed observed set shared by every case (its states vary per case)
-        from synth.bn import sample_cases
         rng = np.random.default_rng(1234)
         observed_set = sorted(int(v) for v in rng.choice(net.n, size=args.observed_set, replace=False))
-        x = sample_cases(net, n_cases, 1.0, seed=rank_evidence_seed(name, rank))
-        ev = np.full_like(x, -1, dtype=np.int32)
-        ev[:, observed_set] = x[:, observed_set]
     query_set = None
     if args.query_set > 0:
         if not observed_set:
@@ -362,8 +363,20 @@ def main():
         rest = [v for v in range(net.n) if v not in observed_set]
         query_set = sorted(int(v) for v in rng.choice(rest, size=args.query_set, replace=False))
 
+    def make_evidence(n):
+        """This rank's own independent batch of n cases (weak scaling)."""
+        if observed_set:
+            from synth.bn import sample_cases
+            x = sample_cases(net, n, 1.0, seed=rank_evidence_seed(name, rank))
+            e = np.full_like(x, -1, dtype=np.int32)
+            e[:, observed_set] = x[:, observed_set]
+            return e
+        return configs.evidence(name, net, n_cases=n, seed=rank_evidence_seed(name, rank))
+
     if args.impl == "reference":
-        return run_reference(args, name, net, ev, rank, world)
+        # the oracle runs bounded samples of the workload; an arena-sized
+        # batch needs a GPU plan to size it, so the sample pool is 1024 cases
+        return run_reference(args, name, net, make_evidence(args.cases or DEFAULT_CASES[name] or 1024), rank, world)
 
     import torch
     if args.serving_only:
@@ -376,15 +389,27 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     import paper_2212_04241_gb300.jt as J
-    # the library's autotuner picks the tile shape for this network and batch
     spec = {"observed_set": observed_set} if observed_set else {}
     if query_set:
         spec["query_set"] = query_set
-    if args.plan:
-        tuned = dict(json.loads(args.plan), **spec)
+    fixed = dict(json.loads(args.plan), **spec) if args.plan else None
+    if arena_sized:
+        # the batch is what one table arena admits under the memory budget
+        probe = J.Plan(net, **(fixed or spec))
+        n_cases = probe.info()["budget_chunk_cases"]
+        probe.close()
+    else:
+        n_cases = args.cases or DEFAULT_CASES[name]
+    # the library's autotuner picks the work shape for this network and batch
+    if fixed is not None:
+        tuned = fixed
     else:
         tuned, _ = J.autotune(net, n_cases, **spec) if not args.no_autotune else (dict(spec), None)
     plan = J.Plan(net, **tuned)
+    if arena_sized:
+        # the tuned tile width may admit a different batch: take its own
+        n_cases = plan.info()["budget_chunk_cases"]
+    ev = make_evidence(n_cases)
     stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
     d_ev = torch.from_numpy(ev).cuda()
@@ -462,11 +487,16 @@ def main():
     kernel = f"k_{dom}_flow" if dataflow else f"k_{dom}"
     # the plan's distribute work-item target (0 in the options = items_per_tile, whose 0 = 192)
     items_d = int(tuned.get("items_per_tile_distribute") or tuned.get("items_per_tile") or 192)
-    traffic = (MEASURED_TRAFFIC.get((name, n_cases, items_d, _kernel_source_hash()))
+    ksha = _kernel_source_hash()
+    traffic = (MEASURED_TRAFFIC.get((name, n_cases, items_d, ksha))
                if dataflow and dom == "distribute" and not observed_set else None)
     roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "launches": prof[f"{dom}_launches"],
+                "traffic": traffic,
+                "traffic_source": (f"stored ncu capture (dram__bytes_read.sum + dram__bytes_write.sum per launch), "
+                                   f"kernel source sha256 {ksha}" if traffic is not None else
+                                   f"no stored ncu capture for kernel source sha256 {ksha} and this plan shape"),
+                "launches": prof[f"{dom}_launches"],
                 "kernel_ms_per_pass": kinds[dom], "other_kernel_ms_per_pass": kinds["collect" if dom == "distribute" else "distribute"],
                 "whole_pass_algorithmic_GBps": info["algorithmic_bytes_per_case"] * n_cases / (prof["total_ms"] / 1e3) / 1e9}
 
@@ -525,13 +555,16 @@ def main():
         return 0
     launches = info["kernels_per_chunk"] * ((n_cases + info["chunk_cases"] - 1) // max(1, info["chunk_cases"]))
     line = {
-        "metric": "evidence cases/sec at <=1e-5 posterior error (batched FP32 path)",
+        "metric": METRIC,
         "value": value, "unit": "cases/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[name] + (f"_observedset{args.observed_set}" if observed_set else "")
                    + (f"_queryset{args.query_set}" if query_set else ""),
                    "observed_set": observed_set, "query_set": query_set, "pruned_vars": info["pruned_vars"], "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
+                   "batch": ("arena-admitted: the cases one table arena holds under the automatic budget "
+                             "(min(224 GiB, 70% of free device memory))" if arena_sized else "fixed"),
+                   "arena_gb": info["arena_bytes"] / 1e9,
                    "chunk_cases": info["chunk_cases"], "levels": info["n_levels"],
                    "autotuned": ({k: tuned.get(k) for k in ("cases_per_thread", "items_per_tile", "items_per_tile_distribute")}
                                  if tuned and not args.plan and not args.no_autotune else None),

@@ -113,6 +113,11 @@ enum {
  * latency. */
 enum { JT_SCHEDULE_DATAFLOW = 0, JT_SCHEDULE_LAYERS = 1 };
 
+/* Number of table-size buckets of the per-bucket work shape: bucket b holds
+ * the tables with 2^b <= entries < 2^(b+1) (a clique for the collect pass,
+ * a distribute task's source rows for the distribute pass). */
+#define JT_SIZE_BUCKETS 32
+
 typedef struct {
   int32_t root_rule;          /* JT_ROOT_* (default JT_ROOT_MIN_HEIGHT) */
   int32_t host_only;          /* 1: compile on the host only, allocate no
@@ -190,6 +195,17 @@ typedef struct {
                                  jt_infer_device, jt_infer_device_noalloc,
                                  jt_profile, jt_autotune), not
                                  jt_infer_plain, jt_infer_cpu or the server. */
+  int32_t collect_rows_by_bucket[JT_SIZE_BUCKETS];
+                              /* rows (table entries) per warp work item of
+                                 the collect pass for the cliques of each
+                                 size bucket (JT_SIZE_BUCKETS); 0 = the
+                                 layer's automatic value (items_per_tile).
+                                 Each value is rounded down to a power of two
+                                 in [16, 4096].  Ignored when rows_per_cta is
+                                 set.  jt_autotune fills these per bucket. */
+  int32_t distribute_rows_by_bucket[JT_SIZE_BUCKETS];
+                              /* the same for the distribute pass, bucketed
+                                 by each task's source rows */
 } jt_compile_opts;
 
 typedef struct {
@@ -215,6 +231,20 @@ typedef struct {
                                  smaller than every clique holding them)
                                  rather than evaluated per clique entry */
   int32_t pruned_vars;          /* barren variables removed (query_set) */
+  int32_t budget_chunk_cases;   /* cases one arena chunk admits under the
+                                   plan's arena budget (arena_bytes, or the
+                                   automatic budget evaluated at this call);
+                                   0 for host_only plans */
+  int32_t collect_rows_by_bucket[JT_SIZE_BUCKETS];    /* rows per collect work
+                                   item used for each size bucket (largest
+                                   value in the bucket; 0 = no clique) */
+  int32_t distribute_rows_by_bucket[JT_SIZE_BUCKETS]; /* the same for the
+                                   distribute tasks */
+  int64_t collect_entries_by_bucket[JT_SIZE_BUCKETS]; /* clique entries per
+                                   case in each bucket (collect work) */
+  int64_t distribute_entries_by_bucket[JT_SIZE_BUCKETS]; /* source rows per
+                                   case of the distribute tasks in each
+                                   bucket */
 } jt_plan_info_t;
 
 /* Fill opts with the defaults listed above. */
@@ -279,8 +309,9 @@ JT_API jt_status jt_infer_device(jt_plan *plan, int32_t n_cases, const int32_t *
  * serving -- a process whose device memory is owned by another allocator,
  * a latency-bound loop that cannot afford cudaMalloc/cudaFree (they
  * synchronise the whole device), or a deployment that forbids allocation
- * after start-up.  Same arguments, results and stream semantics as
- * jt_infer_device; it allocates nothing: the per-batch tables live in one
+ * after start-up.  Same arguments and stream semantics as jt_infer_device,
+ * and the same results bit for bit; it allocates nothing: the per-batch
+ * tables live in one
  * fixed device array of JT_NOALLOC_SCRATCH_BYTES that the library defines
  * (every GPU that loads the library keeps it until the process exits).
  * The first call on a device looks up that array's device address, so make
@@ -290,7 +321,11 @@ JT_API jt_status jt_infer_device(jt_plan *plan, int32_t n_cases, const int32_t *
  * and give wrong results -- serialise them.  A plan whose tables for one
  * case tile (jt_plan_info: tile_cases cases) exceed the array is refused
  * with JT_ENOMEM and a message from jt_last_error; larger batches are run
- * in chunks that fit.
+ * in chunks that fit.  One difference from jt_infer_device: every call
+ * starts with the array's expired-wait flag cleared, so an expired device
+ * wait marks the cases of that call only (JT_CASE_INCOMPLETE) and is not
+ * carried into later calls (jt_infer_device keeps its flag set until a
+ * synchronous call reports it).
  */
 JT_API jt_status jt_infer_device_noalloc(jt_plan *plan, int32_t n_cases, const int32_t *d_evidence,
                                          double *d_log_pe, double *d_posteriors,
@@ -353,6 +388,17 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
 JT_API jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
                              const int32_t *parents, const double *cpt, const jt_compile_opts *base,
                              int32_t n_cases, jt_compile_opts *best, double *best_ns_per_case);
+
+/*
+ * Testing only (no counterpart in the paper): turn the stall compiled into
+ * a plan by jt_compile_opts.stall_clique on (enabled = 1, the state after
+ * jt_compile) or off (0), so that one plan can run a pass whose bounded
+ * device waits expire and then a normal pass on the same per-batch tables.
+ * It rewrites one producer count of the plan's device work description
+ * and synchronises; it must not overlap a pass of the plan.  JT_EINVAL if
+ * the plan was compiled without stall_clique or with host_only.
+ */
+JT_API jt_status jt_debug_stall(jt_plan *plan, int32_t enabled);
 
 /* Sizes and layout of a compiled plan. */
 JT_API jt_status jt_plan_info(const jt_plan *plan, jt_plan_info_t *out);

@@ -136,6 +136,10 @@ void enqueue_passes(const jt_plan *pl, const DevArena &A, cudaStream_t s) {
   const Plan &P = pl->P;
   const ArenaLayout L = arena_layout(P);
   cudaMemsetAsync(A.maxbits, 0, L.maxbits * (size_t)A.tiles, s);
+  // split-sum counters start every chunk at zero: the last piece of a group
+  // resets its counter, but a pass whose bounded wait expired may leave a
+  // group short of its last piece, and the next chunk must not inherit it
+  cudaMemsetAsync(A.counters, 0, L.counters * (size_t)A.tiles, s);
   if (P.opts.schedule == JT_SCHEDULE_LAYERS) {
     for (int l = P.height; l >= 0; --l) enqueue_collect_layer(pl, A, l, s);
     for (int l = 0; l <= P.height; ++l) enqueue_distribute_layer(pl, A, l, s);
@@ -467,6 +471,32 @@ extern "C" jt_status jt_plan_info(const jt_plan *pl, jt_plan_info_t *o) {
   o->pruned_vars = P.n_pruned;
   o->separator_evidence_vars = 0;
   for (const HostClique &C : P.cl) o->separator_evidence_vars += (int32_t)C.ev_sep.size();
+  o->budget_chunk_cases = 0;
+  if (!pl->host_only) {
+    const int t = pl->budget_tiles_cache > 0 ? pl->budget_tiles_cache : budget_tiles(pl, P.opts.arena_bytes);
+    o->budget_chunk_cases = t > 0 ? t * P.tile : 0;
+  }
+  for (int b = 0; b < JT_SIZE_BUCKETS; ++b) {
+    o->collect_rows_by_bucket[b] = P.c_bucket_rows[b];
+    o->distribute_rows_by_bucket[b] = P.d_bucket_rows[b];
+    o->collect_entries_by_bucket[b] = P.c_bucket_entries[b];
+    o->distribute_entries_by_bucket[b] = P.d_bucket_entries[b];
+  }
+  return JT_OK;
+}
+
+extern "C" jt_status jt_debug_stall(jt_plan *pl, int32_t enabled) {
+  if (!pl || pl->host_only) { set_error("bad plan"); return JT_EINVAL; }
+  const Plan &P = pl->P;
+  if (P.opts.stall_clique <= 0) { set_error("the plan was compiled without stall_clique"); return JT_EINVAL; }
+  std::lock_guard<std::mutex> lk(pl->mu);
+  JT_CUDA_TRY(cudaSetDevice(pl->device));
+  const int k = P.opts.stall_clique - 1;
+  // the host copy counts the missing producer; the device copy is the one
+  // the collect pass reads
+  const uint32_t need = P.c_need[k] - (enabled ? 0u : 1u);
+  JT_CUDA_TRY(cudaMemcpy(const_cast<uint32_t *>(pl->dp.c_need) + k, &need, sizeof(need), cudaMemcpyHostToDevice));
+  JT_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
   return JT_OK;
 }
 
@@ -811,6 +841,7 @@ static jt_status jt_profile_impl(jt_plan *pl, int32_t n_cases, const int32_t *d_
     DevArena A = pl->arena.da;
     A.tiles = (nc + W - 1) / W;
     JT_CUDA_TRY(cudaMemsetAsync(A.bad, 0, arena_layout(P).bad * (size_t)A.tiles, s));
+    JT_CUDA_TRY(cudaMemsetAsync(A.counters, 0, arena_layout(P).counters * (size_t)A.tiles, s));
     int e0 = mark();
     launch_evidence(P.cpt_per_thread, d_ev + b * P.io_n, nc, pl->dp, A, s);
     spans.push_back({e0, mark(), 2});

@@ -247,6 +247,17 @@ int64_t append_pool(std::vector<int32_t> &pool, const std::vector<int32_t> &t) {
   return off;
 }
 
+}  // namespace
+
+// Size bucket of a table of `rows` entries: floor(log2(rows)).
+int size_bucket(int64_t rows) {
+  int b = 0;
+  while (b + 1 < JT_SIZE_BUCKETS && (rows >> (b + 1)) > 0) ++b;
+  return b;
+}
+
+namespace {
+
 bool all_zero(const std::vector<int64_t> &w) {
   for (auto x : w)
     if (x) return false;
@@ -810,6 +821,21 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       }
     }
   };
+  // Per size bucket (bucket b: 2^b <= rows < 2^(b+1)) the caller may fix
+  // the rows of a work item; jt_autotune times these per bucket.  A value
+  // is rounded down to a power of two in [16, 4096].
+  auto bucket_rows = [&](const int32_t *table, int64_t rows, int64_t layer_value) -> int64_t {
+    if (opts.rows_per_cta > 0) return layer_value;
+    const int b = size_bucket(rows);
+    if (table[b] <= 0) return layer_value;
+    int64_t r = 16;
+    while (r < 4096 && r * 2 <= table[b]) r *= 2;
+    return r;
+  };
+  P.c_bucket_rows.fill(0);
+  P.d_bucket_rows.fill(0);
+  P.c_bucket_entries.fill(0);
+  P.d_bucket_entries.fill(0);
   P.levels.assign(P.height + 1, Level{});
   for (int L = 0; L <= P.height; ++L) {
     Level &lv = P.levels[L];
@@ -823,14 +849,25 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     const int64_t cR = layer_rows(crows, false), dR = layer_rows(drows, true);
     for (int c = 0; c < m; ++c) {
       if (P.cl[c].depth != L) continue;
-      emit(P.citems, c, P.cl[c].nsep, P.cl[c].R, cR);
+      const int64_t r = bucket_rows(opts.collect_rows_by_bucket, P.cl[c].size, cR);
+      const int b = size_bucket(P.cl[c].size);
+      P.c_bucket_rows[b] = std::max<int32_t>(P.c_bucket_rows[b], (int32_t)r);
+      P.c_bucket_entries[b] += P.cl[c].size;
+      emit(P.citems, c, P.cl[c].nsep, P.cl[c].R, r);
       lv.c_max_maps = std::max(lv.c_max_maps, P.dcl[c].sev_end - P.dcl[c].map_begin);
     }
     lv.c_item_end = (int64_t)P.citems.size();
     lv.d_item_begin = (int64_t)P.ditems.size();
     for (int c = 0; c < m; ++c) {
       if (P.cl[c].depth != L) continue;
-      for (int t : tasks_of[c]) emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U, dR);
+      for (int t : tasks_of[c]) {
+        const int64_t rows = P.dtask[t].T * P.dtask[t].U;
+        const int64_t r = bucket_rows(opts.distribute_rows_by_bucket, rows, dR);
+        const int b = size_bucket(rows);
+        P.d_bucket_rows[b] = std::max<int32_t>(P.d_bucket_rows[b], (int32_t)r);
+        P.d_bucket_entries[b] += rows;
+        emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U, r);
+      }
     }
     lv.d_item_end = (int64_t)P.ditems.size();
   }

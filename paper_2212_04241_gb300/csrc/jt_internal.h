@@ -1,6 +1,7 @@
 // Internal structures shared by the host compiler, the runtime and the kernels.
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <exception>
 #include <new>
@@ -204,6 +205,10 @@ struct Plan {
   std::vector<int32_t> io_post_col;   // kept posterior column -> full-row column
   std::vector<int32_t> io_nan_cols;   // full-row columns of the removed variables
 
+  // rows per work item used in each size bucket, and the entries there
+  std::array<int32_t, JT_SIZE_BUCKETS> c_bucket_rows{}, d_bucket_rows{};
+  std::array<int64_t, JT_SIZE_BUCKETS> c_bucket_entries{}, d_bucket_entries{};
+
   jt_compile_opts opts{};
   int cpt_per_thread = 4;
   int tile = 128;
@@ -218,6 +223,8 @@ jt_status build_plan_pruned(int32_t n, const int32_t *card, const int32_t *pptr,
                             const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err);
 
 void set_error(const std::string &msg);
+// size bucket of a table of `rows` entries: floor(log2(rows)), capped
+int size_bucket(int64_t rows);
 
 // Runs the body of a C entry point: a C++ exception (a failed host
 // allocation, a thread that cannot start) becomes a status, never an abort.

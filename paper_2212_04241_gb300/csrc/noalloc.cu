@@ -61,7 +61,7 @@ static jt_status jt_infer_device_noalloc_impl(jt_plan *pl, int32_t n_cases, cons
   const Plan &P = pl->P;
   const ArenaLayout L = arena_layout(P);
   if (L.bytes(1) > kScratchBytes) {
-    set_error("this plan needs " + std::to_string(L.per_tile) + " bytes of scratch per case tile; "
+    set_error("this plan needs " + std::to_string(L.bytes(1)) + " bytes of scratch for one case tile; "
               "the static scratch holds " + std::to_string(kScratchBytes) + " bytes");
     return JT_ENOMEM;
   }
@@ -82,8 +82,9 @@ static jt_status jt_infer_device_noalloc_impl(jt_plan *pl, int32_t n_cases, cons
   const int W = P.tile;
   const int64_t chunk = (int64_t)tiles * W;
   // the array keeps the previous call's contents: the split-sum counters
-  // and the error flag must start at zero (the other per-chunk state is
-  // cleared below)
+  // and the expired-wait flag must start at zero (so an expired wait of an
+  // earlier call is not carried into this one; the other per-chunk state is
+  // cleared by the passes themselves)
   if (cudaMemsetAsync(a.da.counters, 0, L.counters * (size_t)tiles, s) != cudaSuccess ||
       cudaMemsetAsync(a.da.errflag, 0, sizeof(uint32_t), s) != cudaSuccess) {
     cudaGetLastError();

@@ -19,6 +19,7 @@ JT_OK, JT_EINVAL, JT_ECYCLE, JT_ETOOBIG, JT_ENOMEM, JT_ECUDA, JT_ETIMEOUT, JT_EB
 JT_CASE_OK, JT_CASE_ZERO_EVIDENCE, JT_CASE_BAD_EVIDENCE, JT_CASE_INCOMPLETE = 0, 1, 2, 3
 JT_ROOT_LARGEST, JT_ROOT_MIN_HEIGHT = 0, 1
 JT_SCHEDULE_DATAFLOW, JT_SCHEDULE_LAYERS = 0, 1
+JT_SIZE_BUCKETS = 32
 
 
 class JTError(RuntimeError):
@@ -35,7 +36,9 @@ class CompileOpts(ctypes.Structure):
                 ("items_per_tile_distribute", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("wait_limit_us", ctypes.c_int32), ("stall_clique", ctypes.c_int32),
                 ("n_observed_set", ctypes.c_int32), ("observed_set", ctypes.c_void_p),
-                ("rescale", ctypes.c_int32), ("n_query_set", ctypes.c_int32), ("query_set", ctypes.c_void_p)]
+                ("rescale", ctypes.c_int32), ("n_query_set", ctypes.c_int32), ("query_set", ctypes.c_void_p),
+                ("collect_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
+                ("distribute_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -48,14 +51,23 @@ class PlanInfo(ctypes.Structure):
                 ("collect_items", ctypes.c_int64), ("distribute_items", ctypes.c_int64),
                 ("algorithmic_bytes_per_case", ctypes.c_double),
                 ("kernels_per_chunk", ctypes.c_int32), ("sliced_vars", ctypes.c_int32),
-                ("separator_evidence_vars", ctypes.c_int32), ("pruned_vars", ctypes.c_int32)]
+                ("separator_evidence_vars", ctypes.c_int32), ("pruned_vars", ctypes.c_int32),
+                ("budget_chunk_cases", ctypes.c_int32),
+                ("collect_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
+                ("distribute_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
+                ("collect_entries_by_bucket", ctypes.c_int64 * JT_SIZE_BUCKETS),
+                ("distribute_entries_by_bucket", ctypes.c_int64 * JT_SIZE_BUCKETS)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 EXPORTS = ["jt_default_opts", "jt_compile", "jt_autotune", "jt_infer", "jt_infer_device", "jt_infer_plain", "jt_infer_cpu",
-           "jt_profile",
+           "jt_profile", "jt_debug_stall",
            "jt_plan_info", "jt_plan_clique", "jt_plan_free", "jt_status_string", "jt_last_error",
            "jt_server_create", "jt_server_add_plan", "jt_submit", "jt_poll", "jt_server_drain",
            "jt_server_stats", "jt_server_destroy"]
@@ -76,6 +88,7 @@ def _load():
         "jt_infer_plain": ([P, I32, P, P, P, P, P], ctypes.c_int),
         "jt_infer_cpu": ([P, I32, P, P, P, P, I32], ctypes.c_int),
         "jt_profile": ([P, I32, P, P, P, P, P, P], ctypes.c_int),
+        "jt_debug_stall": ([P, I32], ctypes.c_int),
         "jt_plan_info": ([P, ctypes.POINTER(PlanInfo)], ctypes.c_int),
         "jt_plan_clique": ([P, I32, P, P, P, P], ctypes.c_int),
         "jt_plan_free": ([P], None),
@@ -122,7 +135,12 @@ def default_opts(**kw) -> CompileOpts:
     obs = kw.pop("observed_set", None)
     qry = kw.pop("query_set", None)
     for k, v in kw.items():
-        setattr(o, k, v)
+        if k in ("collect_rows_by_bucket", "distribute_rows_by_bucket"):
+            arr = getattr(o, k)
+            for i, x in enumerate(v):
+                arr[i] = int(x)
+        else:
+            setattr(o, k, v)
     if obs is not None and len(obs) > 0:
         arr = np.ascontiguousarray(obs, dtype=np.int32)
         o._observed_keepalive = arr
@@ -158,6 +176,8 @@ def autotune(net, n_cases: int, **opts):
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
                                            "items_per_tile_distribute", "use_graphs", "arena_bytes",
                                            "max_clique_entries", "schedule", "rescale")}
+    for k in ("collect_rows_by_bucket", "distribute_rows_by_bucket"):
+        out[k] = [int(x) for x in getattr(best, k)]
     for k in ("observed_set", "query_set"):
         if opts.get(k) is not None:
             out[k] = list(opts[k])
@@ -257,6 +277,10 @@ class Plan:
         s = None if stream is None else ctypes.c_void_p(int(stream))
         _check(lib.jt_infer_device(self._h, int(n_cases), _ptr(d_evidence), _ptr(d_log_pe), _ptr(d_post),
                                    _ptr(d_status), s))
+
+    def debug_stall(self, enabled: bool):
+        """Testing hook (jt_debug_stall): turn the compiled stall_clique stall on or off."""
+        _check(lib.jt_debug_stall(self._h, 1 if enabled else 0))
 
     def profile(self, d_evidence, d_log_pe, d_post, d_status, n_cases=None, stream=None):
         """Instrumented run (jt_profile): per-kernel-type device milliseconds."""

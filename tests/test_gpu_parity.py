@@ -319,3 +319,53 @@ def test_expired_wait_reports_timeout_and_context_stays_usable():
     assert np.all(d_st.cpu().numpy() == J.JT_CASE_INCOMPLETE)
     assert np.all(np.isnan(d_lp.cpu().numpy()))
     assert_parity32(*good.infer(ev), *_oracle(net, ev), where="after an expired wait")
+
+
+@pytest.mark.parametrize("which", ["root", "leaf"])
+def test_same_plan_recovers_after_expired_wait(which):
+    """A pass whose bounded waits expire may leave split-sum counters and
+    per-tile state behind in the plan's arena; the next pass on the SAME
+    plan and arena must start clean and match the oracle.  The stall is
+    turned on and off on one plan (jt_debug_stall); short items make many
+    split segments, whose counters a failed pass can leave short."""
+    net = configs.network("bn60")
+    ev = configs.evidence("bn60", net, n_cases=300)
+    probe = J.Plan(net, host_only=1)
+    info = probe.info()
+    if which == "root":
+        k = info["root"]
+    else:
+        depth = [probe.clique(c)[2] for c in range(info["n_cliques"])]
+        k = int(np.argmax(depth))
+    plan = J.Plan(net, stall_clique=k + 1, wait_limit_us=2000, items_per_tile=1536,
+                  items_per_tile_distribute=1536)
+    expect = _oracle(net, ev)
+    for _ in range(2):
+        with pytest.raises(J.JTError) as e:
+            plan.infer(ev)                       # stalled: the waits expire
+        assert e.value.status == J.JT_ETIMEOUT
+        plan.debug_stall(False)
+        assert_parity32(*plan.infer(ev), *expect, where=f"stall on clique {k} lifted")
+        # the device path: a stalled call marks its cases, the next
+        # synchronous call reports the expired wait and clears it
+        plan.debug_stall(True)
+        d_ev = torch.from_numpy(ev).cuda()
+        d_lp = torch.empty(300, dtype=torch.float64, device="cuda")
+        d_post = torch.empty((300, plan.sum_card), dtype=torch.float64, device="cuda")
+        d_st = torch.empty(300, dtype=torch.int32, device="cuda")
+        plan.infer_device(d_ev, d_lp, d_post, d_st, stream=torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert np.all(d_st.cpu().numpy() == J.JT_CASE_INCOMPLETE)
+        with pytest.raises(J.JTError) as e:
+            plan.infer(ev)
+        assert e.value.status == J.JT_ETIMEOUT
+        plan.debug_stall(False)
+        assert_parity32(*plan.infer(ev), *expect, where=f"device path, stall on clique {k} lifted")
+        plan.debug_stall(True)
+
+
+def test_debug_stall_needs_a_stall_plan():
+    net = configs.network("bn20")
+    with pytest.raises(J.JTError) as e:
+        J.Plan(net).debug_stall(False)
+    assert e.value.status == J.JT_EINVAL

@@ -3,7 +3,8 @@
 The no-allocation variant is for callers that cannot allocate device memory
 while serving (memory owned by another allocator, loops that cannot afford
 cudaMalloc's device-wide synchronisation, no allocation after start-up).
-It must give the same outputs as the regular entry point, call after call,
+It runs the same kernels in the same order as the regular entry point, so
+its outputs must equal that entry point's bit for bit, call after call,
 although every call reuses the same fixed device array.  This file is named
 to be collected last.
 """
@@ -61,6 +62,10 @@ def test_noalloc_matches_regular_entry_point_twice(name, n_cases, cpt):
         torch.cuda.synchronize()
         lp, post, st = (t.cpu().numpy() for t in out)
         assert np.array_equal(st, rst), f"call {call}: status mismatch"
+        # the same kernels in the same order: bitwise equal (the tolerance
+        # check states the bound the library promises in any case)
+        assert np.array_equal(lp, rlp, equal_nan=True), f"call {call}: log P(e) differs"
+        assert np.array_equal(post, rpost, equal_nan=True), f"call {call}: posteriors differ"
         ok = rst == 0
         assert np.max(np.abs(post[ok] - rpost[ok])) <= POST_TOL32, f"call {call}"
         assert max_logpe_err(lp[ok], rlp[ok]) <= LOGPE_REL32, f"call {call}"
