@@ -98,6 +98,18 @@ def _cpu_layers_rate(plan, ev, seconds=1.5):
             "sample": f"first {m} cases per thread count"}
 
 
+def _bucket_table(info):
+    """Rows per warp work item used in each table-size bucket (bucket b:
+    2^b <= rows < 2^(b+1)) and the share of each pass's rows it holds."""
+    out = {}
+    for pas in ("collect", "distribute"):
+        ent = info[f"{pas}_entries_by_bucket"]
+        tot = float(sum(ent)) or 1.0
+        out[pas] = {str(b): {"rows_per_item": info[f"{pas}_rows_by_bucket"][b], "share": round(e / tot, 4)}
+                    for b, e in enumerate(ent) if e}
+    return out
+
+
 def _kernel_source_hash():
     import hashlib
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2212_04241_gb300", "csrc", "kernels.cu")
@@ -568,6 +580,7 @@ def main():
                    "chunk_cases": info["chunk_cases"], "levels": info["n_levels"],
                    "autotuned": ({k: tuned.get(k) for k in ("cases_per_thread", "items_per_tile", "items_per_tile_distribute")}
                                  if tuned and not args.plan and not args.no_autotune else None),
+                   "work_shape_by_bucket": _bucket_table(info),
                    "plan_options": tuned if args.plan else None,
                    "schedule": "dataflow" if dataflow else "layers",
                    "sum_clique_entries": info["sum_clique_entries"],

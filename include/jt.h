@@ -375,15 +375,25 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
                             void *cuda_stream, double *out);
 
 /*
- * Autotuner (no counterpart in the paper): compiles the network with each
- * candidate tile shape -- cases per thread in {4, 8} and work items per
- * tile and layer in {96, 192, 384, 768, 1536} -- times the collect and the distribute
- * launches of n_cases cases separately on the current device (jt_profile,
- * best of three runs after a warm-up) in base's schedule, picks per tile
- * width the best items value of each pass, and writes the fastest
- * combination to *best (base fields kept) and its pass time per case in ns
- * to *best_ns_per_case (may be NULL).  base may be NULL for the defaults.
- * Allocates and frees its own device memory.
+ * Autotuner (no counterpart in the paper; it addresses the load imbalance
+ * between threads that Section 2 attributes to tables of very different
+ * sizes).  Times the collect and the distribute launches of n_cases cases
+ * separately on the current device (jt_profile: one warm-up run, then the
+ * best of two) in base's schedule, in two stages:
+ *   1. per tile width (cases per thread 4 and 8, unless base fixes it) the
+ *      work-item target of each pass over {96, 192, 384, 768, 1536} items
+ *      per tile and layer; the fastest width and targets are kept;
+ *   2. per table-size bucket (JT_SIZE_BUCKETS; the buckets holding at
+ *      least 2 % of a pass's rows, largest first, at most eight) the rows
+ *      of one warp work item -- hence the warps (threads) per table and
+ *      the tile shape rows x cases -- over the powers of two 32 .. 4096,
+ *      each pass keeping its own best value (coordinate descent; a change
+ *      is kept when it is at least 1 % faster).
+ * Between candidates only the work lists are rebuilt, not the plan.
+ * Writes the result to *best (base fields kept; the bucket tables in
+ * collect_rows_by_bucket / distribute_rows_by_bucket) and its pass time per
+ * case in ns to *best_ns_per_case (may be NULL).  base may be NULL for the
+ * defaults.  Allocates and frees its own device memory.
  */
 JT_API jt_status jt_autotune(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
                              const int32_t *parents, const double *cpt, const jt_compile_opts *base,

@@ -53,6 +53,7 @@ void arena_free(Arena &a) {
   if (a.mem && a.owns) cudaFree(a.mem);
   a.mem = nullptr;
   a.bytes = 0;
+  a.alloc_bytes = 0;
   a.tiles = 0;
 }
 
@@ -95,6 +96,7 @@ jt_status arena_alloc(const Plan &P, Arena &a, int tiles) {
   }
   a.owns = true;
   arena_bind(P, a, static_cast<char *>(mem), tiles);
+  a.alloc_bytes = L.bytes(tiles);
   // counters start at zero; every combining warp resets its own counter.
   // cudaMemset runs on the legacy default stream, which does not order the
   // library's non-blocking streams: wait for it before any batch can use
@@ -114,6 +116,7 @@ jt_status arena_wrap(const Plan &P, Arena &a, void *mem, size_t bytes, int tiles
   }
   a.owns = false;
   arena_bind(P, a, static_cast<char *>(mem), tiles);
+  a.alloc_bytes = bytes;
   return JT_OK;
 }
 
@@ -267,6 +270,39 @@ static size_t put(std::vector<char> &blob, const std::vector<T> &v) {
   return off;
 }
 
+// The work lists (items of both passes, flow layers, producer counts) live
+// in their own device block so that retile can replace them.
+static jt_status upload_work(jt_plan *pl) {
+  Plan &P = pl->P;
+  std::vector<char> blob;
+  const size_t o_ci = put(blob, P.citems), o_di = put(blob, P.ditems);
+  const size_t o_cfp = put(blob, P.c_flow_pref), o_cfb = put(blob, P.c_flow_begin);
+  const size_t o_dfp = put(blob, P.d_flow_pref), o_dfb = put(blob, P.d_flow_begin);
+  const size_t o_cn = put(blob, P.c_need), o_cno = put(blob, P.c_notify), o_dn = put(blob, P.d_need);
+  if (pl->d_work) {
+    cudaFree(pl->d_work);
+    pl->d_work = nullptr;
+  }
+  JT_CUDA_TRY(cudaMalloc(&pl->d_work, blob.size()));
+  pl->work_bytes = blob.size();
+  JT_CUDA_TRY(cudaMemcpy(pl->d_work, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  JT_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));  // see upload_plan
+  char *b = static_cast<char *>(pl->d_work);
+  DevPlan &D = pl->dp;
+  D.citems = reinterpret_cast<const DItem *>(b + o_ci);
+  D.ditems = reinterpret_cast<const DItem *>(b + o_di);
+  D.c_flow_pref = reinterpret_cast<const int64_t *>(b + o_cfp);
+  D.c_flow_begin = reinterpret_cast<const int64_t *>(b + o_cfb);
+  D.d_flow_pref = reinterpret_cast<const int64_t *>(b + o_dfp);
+  D.d_flow_begin = reinterpret_cast<const int64_t *>(b + o_dfb);
+  D.c_need = reinterpret_cast<const uint32_t *>(b + o_cn);
+  D.c_notify = reinterpret_cast<const int32_t *>(b + o_cno);
+  D.d_need = reinterpret_cast<const uint32_t *>(b + o_dn);
+  D.n_partials = std::max<int64_t>(1, P.n_partials);
+  D.n_groups = std::max<int64_t>(1, P.n_groups);
+  return JT_OK;
+}
+
 static jt_status upload_plan(jt_plan *pl) {
   Plan &P = pl->P;
   // the kernels index evidence and posterior rows with these sizes
@@ -282,13 +318,10 @@ static jt_status upload_plan(jt_plan *pl) {
   std::vector<char> blob;
   std::vector<int32_t> card32(P.card.begin(), P.card.end());
   const size_t o_cl = put(blob, P.dcl), o_map = put(blob, P.dmap), o_task = put(blob, P.dtask);
-  const size_t o_ci = put(blob, P.citems), o_di = put(blob, P.ditems), o_ip = put(blob, P.ipool);
+  const size_t o_ip = put(blob, P.ipool);
   const size_t o_b32 = put(blob, P.base32), o_card = put(blob, card32), o_po = put(blob, P.post_off);
   const size_t o_cp = put(blob, P.comp_ptr), o_cv = put(blob, P.comp_vars), o_cc = put(blob, P.comp_cliques);
   const size_t o_cr = put(blob, P.comp_roots), o_pg = put(blob, P.pgroup_ptr), o_co = put(blob, P.comp_owner);
-  const size_t o_cfp = put(blob, P.c_flow_pref), o_cfb = put(blob, P.c_flow_begin);
-  const size_t o_dfp = put(blob, P.d_flow_pref), o_dfb = put(blob, P.d_flow_begin);
-  const size_t o_cn = put(blob, P.c_need), o_cno = put(blob, P.c_notify), o_dn = put(blob, P.d_need);
   const size_t o_sv = put(blob, P.slice_var);
   const size_t o_cvo = put(blob, P.comp_var_owner);
   const size_t o_iv = put(blob, P.io_var), o_id = put(blob, P.io_dropped);
@@ -304,8 +337,6 @@ static jt_status upload_plan(jt_plan *pl) {
   D.cl = reinterpret_cast<const DClique *>(b + o_cl);
   D.maps = reinterpret_cast<const DMap *>(b + o_map);
   D.tasks = reinterpret_cast<const DTask *>(b + o_task);
-  D.citems = reinterpret_cast<const DItem *>(b + o_ci);
-  D.ditems = reinterpret_cast<const DItem *>(b + o_di);
   D.ipool = reinterpret_cast<const int32_t *>(b + o_ip);
   D.base32 = reinterpret_cast<const float *>(b + o_b32);
   D.card = reinterpret_cast<const int32_t *>(b + o_card);
@@ -320,13 +351,6 @@ static jt_status upload_plan(jt_plan *pl) {
   D.n_comp_cliques = (int32_t)P.comp_cliques.size();
   D.n_comp = (int32_t)P.comp_roots.size();
   D.pgroup_ptr = reinterpret_cast<const int32_t *>(b + o_pg);
-  D.c_flow_pref = reinterpret_cast<const int64_t *>(b + o_cfp);
-  D.c_flow_begin = reinterpret_cast<const int64_t *>(b + o_cfb);
-  D.d_flow_pref = reinterpret_cast<const int64_t *>(b + o_dfp);
-  D.d_flow_begin = reinterpret_cast<const int64_t *>(b + o_dfb);
-  D.c_need = reinterpret_cast<const uint32_t *>(b + o_cn);
-  D.c_notify = reinterpret_cast<const int32_t *>(b + o_cno);
-  D.d_need = reinterpret_cast<const uint32_t *>(b + o_dn);
   D.slice_var = P.n_sliced > 0 ? reinterpret_cast<const int32_t *>(b + o_sv) : nullptr;
   const bool pruned = P.n_pruned > 0;
   D.io_var = pruned ? reinterpret_cast<const int32_t *>(b + o_iv) : nullptr;
@@ -337,6 +361,8 @@ static jt_status upload_plan(jt_plan *pl) {
   D.io_n = P.io_n;
   D.n_dropped = (int32_t)P.io_dropped.size();
   D.n_nan_cols = (int32_t)P.io_nan_cols.size();
+  jt_status wst = upload_work(pl);
+  if (wst != JT_OK) return wst;
   D.n_flow_layers = P.height + 1;
   D.rescale = P.opts.rescale;
   D.wait_limit_ns = 1000ull * (uint64_t)(P.opts.wait_limit_us > 0 ? P.opts.wait_limit_us : 2000000);
@@ -369,6 +395,46 @@ static jt_status upload_plan(jt_plan *pl) {
   pl->flow_distribute_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, false, false, 0);
   return JT_OK;
 }
+
+namespace jt {
+jt_status retile(jt_plan *pl, const jt_compile_opts &shape) {
+  Plan &P = pl->P;
+  jt_compile_opts o = P.opts;
+  o.items_per_tile = shape.items_per_tile;
+  o.items_per_tile_distribute = shape.items_per_tile_distribute;
+  o.rows_per_cta = shape.rows_per_cta;
+  std::memcpy(o.collect_rows_by_bucket, shape.collect_rows_by_bucket, sizeof(o.collect_rows_by_bucket));
+  std::memcpy(o.distribute_rows_by_bucket, shape.distribute_rows_by_bucket, sizeof(o.distribute_rows_by_bucket));
+  std::string err;
+  jt_status st = emit_work(P, o, err);
+  if (st != JT_OK) {
+    set_error(err);
+    return st;
+  }
+  P.opts = o;
+  // captured graphs hold the old work lists' addresses
+  for (auto &kv : pl->arena.graphs) cudaGraphExecDestroy(kv.second);
+  pl->arena.graphs.clear();
+  st = upload_work(pl);
+  if (st != JT_OK) return st;
+  pl->budget_tiles_cache = 0;
+  if (pl->arena.mem) {
+    const ArenaLayout L = arena_layout(P);
+    if (pl->arena.owns && L.bytes(pl->arena.tiles) <= pl->arena.alloc_bytes) {
+      // the new layout fits the allocation: rebind in place
+      char *mem = static_cast<char *>(pl->arena.mem);
+      const size_t alloc = pl->arena.alloc_bytes;
+      arena_bind(P, pl->arena, mem, pl->arena.tiles);
+      pl->arena.alloc_bytes = alloc;
+      JT_CUDA_TRY(cudaMemset(pl->arena.da.errflag, 0, sizeof(uint32_t)));
+      JT_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
+    } else {
+      arena_free(pl->arena);
+    }
+  }
+  return JT_OK;
+}
+}  // namespace jt
 
 extern "C" jt_status jt_compile(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
                                 const int32_t *parents, const double *cpt, const jt_compile_opts *opts,
@@ -431,6 +497,7 @@ extern "C" void jt_plan_free(jt_plan *pl) {
     free_io(pl);
     if (pl->d_plain) cudaFree(pl->d_plain);
     if (pl->d_static) cudaFree(pl->d_static);
+    if (pl->d_work) cudaFree(pl->d_work);
     if (pl->stream) cudaStreamDestroy(pl->stream);
     if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
   }
@@ -908,6 +975,15 @@ extern "C" jt_status jt_profile(jt_plan *pl, int32_t n_cases, const int32_t *d_e
 // ---------------------------------------------------------------------------
 // autotuner: time candidate tile shapes on the caller's batch size
 // ---------------------------------------------------------------------------
+// Two stages, both timed with jt_profile on the caller's batch size (one
+// warm-up run, then the best of two): (1) per tile width (cases per thread
+// 4 and 8) the work-item target of each pass over {96 .. 1536} items per
+// tile and layer; (2) on the best width, per table-size bucket (in order of
+// the rows the bucket holds, those with at least 2 % of a pass's rows, at
+// most eight), the rows of one warp work item over powers of two from 32
+// to 4096, each pass keeping its own best value per bucket (coordinate
+// descent; a change is kept when it is at least 1 % faster).  Only the
+// work lists are rebuilt between candidates (retile), not the plan.
 static jt_status jt_autotune_impl(int32_t n_vars, const int32_t *card, const int32_t *parent_ptr,
                                  const int32_t *parents, const double *cpt, const jt_compile_opts *base,
                                  int32_t n_cases, jt_compile_opts *best, double *best_ns_per_case) {
@@ -934,45 +1010,108 @@ static jt_status jt_autotune_impl(int32_t n_vars, const int32_t *card, const int
   // all variables unobserved: the timing does not depend on the evidence values
   cudaMemset(d_ev, 0xff, sizeof(int32_t) * (size_t)n_cases * n_vars);
   cudaStreamSynchronize(cudaStreamLegacy);  // filled before the plans' streams read it
+  auto time_plan = [&](jt_plan *pl, double &c_ms, double &d_ms) -> jt_status {
+    double out[6];
+    c_ms = d_ms = -1;
+    for (int r = 0; r < 3; ++r) {
+      jt_status st = jt_profile(pl, n_cases, d_ev, d_lp, d_post, d_st, pl->stream, out);
+      if (st != JT_OK) return st;
+      if (r > 0) {  // the first run warms up
+        c_ms = (c_ms < 0) ? out[0] : std::min(c_ms, out[0]);
+        d_ms = (d_ms < 0) ? out[1] : std::min(d_ms, out[1]);
+      }
+    }
+    return JT_OK;
+  };
+  auto shape_of = [](const jt_compile_opts &o) { return o; };
   jt_status result = JT_OK;
   double best_total = -1;
   jt_compile_opts best_o = b;
+  int best_cw = 0;
+  // stage 1: tile width x work-item target per pass
   for (int ci = 0; result == JT_OK && ci < 2; ++ci) {
     if (base && base->cases_per_thread != 0 && ci > 0) break;  // the caller fixed the tile width
     const int cw = (base && base->cases_per_thread != 0) ? base->cases_per_thread : cpts[ci];
+    jt_compile_opts o = b;
+    o.cases_per_thread = cw;
+    o.rows_per_cta = 0;
+    std::memset(o.collect_rows_by_bucket, 0, sizeof(o.collect_rows_by_bucket));
+    std::memset(o.distribute_rows_by_bucket, 0, sizeof(o.distribute_rows_by_bucket));
+    jt_plan *pl = nullptr;
+    jt_status st = jt_compile(n_vars, card, parent_ptr, parents, cpt, &o, &pl);
+    if (st != JT_OK) { result = st; break; }
     double best_c = -1, best_d = -1;
     int item_c = 192, item_d = 192;
-    for (int ii = 0; result == JT_OK && ii < (int)(sizeof(items) / sizeof(items[0])); ++ii) {
-      jt_compile_opts o = b;
-      o.cases_per_thread = cw;
-      o.items_per_tile = items[ii];
-      o.items_per_tile_distribute = items[ii];
-      o.rows_per_cta = 0;
-      jt_plan *pl = nullptr;
-      jt_status st = jt_compile(n_vars, card, parent_ptr, parents, cpt, &o, &pl);
-      if (st != JT_OK) { result = st; break; }
-      double c_ms = -1, d_ms = -1, out[6];
-      for (int r = 0; r < 4 && st == JT_OK; ++r) {
-        st = jt_profile(pl, n_cases, d_ev, d_lp, d_post, d_st, pl->stream, out);
-        if (st == JT_OK && r > 0) {  // first run warms up
-          c_ms = (c_ms < 0) ? out[0] : std::min(c_ms, out[0]);
-          d_ms = (d_ms < 0) ? out[1] : std::min(d_ms, out[1]);
-        }
-      }
-      jt_plan_free(pl);
-      if (st != JT_OK) { result = st; break; }
+    for (int ii = 0; st == JT_OK && ii < (int)(sizeof(items) / sizeof(items[0])); ++ii) {
+      jt_compile_opts sh = shape_of(o);
+      sh.items_per_tile = items[ii];
+      sh.items_per_tile_distribute = items[ii];
+      double c_ms, d_ms;
+      st = retile(pl, sh);
+      if (st == JT_OK) st = time_plan(pl, c_ms, d_ms);
+      if (st != JT_OK) break;
       if (best_c < 0 || c_ms < best_c) { best_c = c_ms; item_c = items[ii]; }
       if (best_d < 0 || d_ms < best_d) { best_d = d_ms; item_d = items[ii]; }
     }
-    if (result != JT_OK) break;
+    jt_plan_free(pl);
+    if (st != JT_OK) { result = st; break; }
     if (best_total < 0 || best_c + best_d < best_total) {
       best_total = best_c + best_d;
-      best_o = b;
-      best_o.cases_per_thread = cw;
+      best_o = o;
       best_o.items_per_tile = item_c;
       best_o.items_per_tile_distribute = item_d;
-      best_o.rows_per_cta = 0;
+      best_cw = cw;
     }
+  }
+  // stage 2: rows per work item per table-size bucket, on the best width
+  if (result == JT_OK && best_cw > 0) {
+    jt_plan *pl = nullptr;
+    jt_status st = jt_compile(n_vars, card, parent_ptr, parents, cpt, &best_o, &pl);
+    double cur_c = -1, cur_d = -1;
+    if (st == JT_OK) st = time_plan(pl, cur_c, cur_d);
+    if (st == JT_OK) {
+      const Plan &P = pl->P;
+      int64_t ctot = 0, dtot = 0;
+      for (int k = 0; k < JT_SIZE_BUCKETS; ++k) { ctot += P.c_bucket_entries[k]; dtot += P.d_bucket_entries[k]; }
+      std::vector<std::pair<double, int>> order;
+      for (int k = 0; k < JT_SIZE_BUCKETS; ++k) {
+        const double w = std::max(ctot ? (double)P.c_bucket_entries[k] / ctot : 0.0,
+                                  dtot ? (double)P.d_bucket_entries[k] / dtot : 0.0);
+        if (w >= 0.02) order.push_back({-w, k});
+      }
+      std::sort(order.begin(), order.end());
+      if (order.size() > 8) order.resize(8);
+      // starting point: the per-layer values of stage 1 (table entries 0)
+      jt_compile_opts sh = best_o;
+      const std::array<int64_t, JT_SIZE_BUCKETS> ce = P.c_bucket_entries, de = P.d_bucket_entries;
+      const int cand[] = {32, 64, 128, 256, 512, 1024, 2048, 4096};
+      for (const auto &wk : order) {
+        const int k = wk.second;
+        const bool tune_c = ctot && (double)ce[k] / ctot >= 0.02, tune_d = dtot && (double)de[k] / dtot >= 0.02;
+        int keep_c = sh.collect_rows_by_bucket[k], keep_d = sh.distribute_rows_by_bucket[k];
+        for (int r : cand) {
+          if (r > (int64_t(2) << k)) break;  // an item cannot outgrow the bucket's tables
+          jt_compile_opts t = sh;
+          if (tune_c) t.collect_rows_by_bucket[k] = r;
+          if (tune_d) t.distribute_rows_by_bucket[k] = r;
+          double c_ms, d_ms;
+          st = retile(pl, t);
+          if (st == JT_OK) st = time_plan(pl, c_ms, d_ms);
+          if (st != JT_OK) break;
+          if (tune_c && c_ms < 0.99 * cur_c) { cur_c = c_ms; keep_c = r; }
+          if (tune_d && d_ms < 0.99 * cur_d) { cur_d = d_ms; keep_d = r; }
+        }
+        if (st != JT_OK) break;
+        sh.collect_rows_by_bucket[k] = keep_c;
+        sh.distribute_rows_by_bucket[k] = keep_d;
+      }
+      if (st == JT_OK) {
+        best_o = sh;
+        best_total = cur_c + cur_d;
+      }
+    }
+    if (pl) jt_plan_free(pl);
+    if (st != JT_OK) result = st;
   }
   cudaFree(d_ev);
   cudaFree(d_lp);

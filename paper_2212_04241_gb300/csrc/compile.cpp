@@ -267,6 +267,173 @@ bool all_zero(const std::vector<int64_t> &w) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// work lists: per-layer warp work items of both passes, the dataflow
+// schedule's flow layers and producer counts.  Depends only on the tree,
+// the tasks and the work-shape options, so a compiled plan can be given a
+// new work shape (jt_autotune's per-bucket tuning) without recompiling.
+// ---------------------------------------------------------------------------
+jt_status emit_work(Plan &P, const jt_compile_opts &opts, std::string &err) {
+  const int m = (int)P.cl.size();
+  // distribute tasks of each clique, in creation order
+  std::vector<std::vector<int>> tasks_of(m);
+  for (int t = 0; t < (int)P.dtask.size(); ++t) tasks_of[P.dtask[t].clique].push_back(t);
+  const int NW = 8;  // warps per block
+  // Rows per warp item: fixed by the option (rows per block / warps), else
+  // chosen per layer so that a layer has about items_per_tile (default 192)
+  // warp items per case tile, between a minimum (32 rows, one index batch,
+  // for collect; 16 for distribute, whose rows carry less work) and 512: a
+  // small layer is latency-bound and finishes sooner in short items, a big
+  // one amortises each item's set-up over long ones.
+  P.rows_per_cta = opts.rows_per_cta > 0 ? opts.rows_per_cta : 0;
+  auto layer_rows = [&](int64_t total, bool distribute) -> int64_t {
+    if (opts.rows_per_cta > 0) return std::max<int64_t>(1, opts.rows_per_cta / NW);
+    int64_t items = opts.items_per_tile > 0 ? opts.items_per_tile : 192;
+    if (distribute && opts.items_per_tile_distribute > 0) items = opts.items_per_tile_distribute;
+    int64_t r = distribute ? 16 : 32;
+    while (r < 512 && r * 2 * items <= total) r *= 2;
+    return r;
+  };
+  P.citems.clear();
+  P.ditems.clear();
+  P.n_groups = 0;
+  P.n_partials = 0;
+  // one item per warp: whole segments when a segment fits the warp's rows,
+  // else the segment is split into pieces combined in piece order
+  auto emit = [&](std::vector<DItem> &out, int task, int64_t nseg, int64_t rows, int64_t ROWS) {
+    if (rows <= ROWS) {
+      int64_t per = std::max<int64_t>(1, ROWS / rows);
+      for (int64_t t0 = 0; t0 < nseg; t0 += per) {
+        DItem it{};
+        it.t0 = t0;
+        it.nt = std::min(per, nseg - t0);
+        it.u0 = 0;
+        it.nu = rows;
+        it.task = task;
+        it.split = 0;
+        it.npieces = 1;
+        it.piece = 0;
+        it.group = -1;
+        it.partial = -1;
+        out.push_back(it);
+      }
+    } else {
+      int64_t np = (rows + ROWS - 1) / ROWS;
+      int64_t per = (rows + np - 1) / np;
+      np = (rows + per - 1) / per;
+      for (int64_t s = 0; s < nseg; ++s) {
+        int32_t group = -1, first = -1;
+        if (np > 1) {
+          group = (int32_t)P.n_groups++;
+          first = (int32_t)P.n_partials;
+          P.n_partials += np;
+        }
+        for (int64_t p = 0; p < np; ++p) {
+          DItem it{};
+          it.t0 = s;
+          it.nt = 1;
+          it.u0 = p * per;
+          it.nu = std::min(per, rows - p * per);
+          it.task = task;
+          it.split = 1;
+          it.npieces = (int32_t)np;
+          it.piece = (int32_t)p;
+          it.group = group;
+          it.partial = np > 1 ? first + (int32_t)p : -1;
+          out.push_back(it);
+        }
+      }
+    }
+  };
+  // Per size bucket (bucket b: 2^b <= rows < 2^(b+1)) the caller may fix
+  // the rows of a work item; jt_autotune times these per bucket.  A value
+  // is rounded down to a power of two in [16, 4096].
+  auto bucket_rows = [&](const int32_t *table, int64_t rows, int64_t layer_value) -> int64_t {
+    if (opts.rows_per_cta > 0) return layer_value;
+    const int b = size_bucket(rows);
+    if (table[b] <= 0) return layer_value;
+    int64_t r = 16;
+    while (r < 4096 && r * 2 <= table[b]) r *= 2;
+    return r;
+  };
+  P.c_bucket_rows.fill(0);
+  P.d_bucket_rows.fill(0);
+  P.c_bucket_entries.fill(0);
+  P.d_bucket_entries.fill(0);
+  P.levels.assign(P.height + 1, Level{});
+  for (int L = 0; L <= P.height; ++L) {
+    Level &lv = P.levels[L];
+    lv.c_item_begin = (int64_t)P.citems.size();
+    int64_t crows = 0, drows = 0;
+    for (int c = 0; c < m; ++c) {
+      if (P.cl[c].depth != L) continue;
+      crows += P.cl[c].size;
+      for (int t : tasks_of[c]) drows += P.dtask[t].T * P.dtask[t].U;
+    }
+    const int64_t cR = layer_rows(crows, false), dR = layer_rows(drows, true);
+    for (int c = 0; c < m; ++c) {
+      if (P.cl[c].depth != L) continue;
+      const int64_t r = bucket_rows(opts.collect_rows_by_bucket, P.cl[c].size, cR);
+      const int b = size_bucket(P.cl[c].size);
+      P.c_bucket_rows[b] = std::max<int32_t>(P.c_bucket_rows[b], (int32_t)r);
+      P.c_bucket_entries[b] += P.cl[c].size;
+      emit(P.citems, c, P.cl[c].nsep, P.cl[c].R, r);
+      lv.c_max_maps = std::max(lv.c_max_maps, P.dcl[c].sev_end - P.dcl[c].map_begin);
+    }
+    lv.c_item_end = (int64_t)P.citems.size();
+    lv.d_item_begin = (int64_t)P.ditems.size();
+    for (int c = 0; c < m; ++c) {
+      if (P.cl[c].depth != L) continue;
+      for (int t : tasks_of[c]) {
+        const int64_t rows = P.dtask[t].T * P.dtask[t].U;
+        const int64_t r = bucket_rows(opts.distribute_rows_by_bucket, rows, dR);
+        const int b = size_bucket(rows);
+        P.d_bucket_rows[b] = std::max<int32_t>(P.d_bucket_rows[b], (int32_t)r);
+        P.d_bucket_entries[b] += rows;
+        emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U, r);
+      }
+    }
+    lv.d_item_end = (int64_t)P.ditems.size();
+  }
+  // dataflow schedule: flow layers (collect deepest first, distribute from
+  // the root) and each clique's producers on its tile
+  P.c_flow_pref.assign(1, 0);
+  P.d_flow_pref.assign(1, 0);
+  P.c_flow_begin.clear();
+  P.d_flow_begin.clear();
+  for (int k = 0; k <= P.height; ++k) {
+    const Level &lc = P.levels[P.height - k];
+    P.c_flow_begin.push_back(lc.c_item_begin);
+    P.c_flow_pref.push_back(P.c_flow_pref.back() + (lc.c_item_end - lc.c_item_begin));
+    const Level &ld = P.levels[k];
+    P.d_flow_begin.push_back(ld.d_item_begin);
+    P.d_flow_pref.push_back(P.d_flow_pref.back() + (ld.d_item_end - ld.d_item_begin));
+  }
+  P.c_need.assign(m, 0);
+  P.d_need.assign(m, 0);
+  P.c_notify.assign(m, -1);
+  for (const DItem &it : P.citems) {
+    const HostClique &K = P.cl[it.task];
+    if (K.parent >= 0 && K.n_up > 0) {
+      P.c_notify[it.task] = K.parent;
+      ++P.c_need[K.parent];
+    }
+  }
+  for (const DItem &it : P.ditems) {
+    const DTask &T = P.dtask[it.task];
+    if (T.kind == TASK_CHILD) ++P.d_need[T.dst];
+  }
+  if (opts.stall_clique > 0) {
+    if (opts.stall_clique > m) {
+      err = "stall_clique out of range";
+      return JT_EINVAL;
+    }
+    ++P.c_need[opts.stall_clique - 1];  // a producer that never comes
+  }
+
+  return JT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // build_plan
 // ---------------------------------------------------------------------------
 jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
@@ -751,161 +918,8 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     for (int v : C.owned_sep) make_task(std::vector<int>{v}, TASK_POSTERIOR, v, P.post_off[v], true);
   }
 
-  // ---------------------------------------------------------------------
-  // per-layer thread-block lists
-  // ---------------------------------------------------------------------
-  const int NW = 8;  // warps per block
-  // Rows per warp item: fixed by the option (rows per block / warps), else
-  // chosen per layer so that a layer has about items_per_tile (default 192)
-  // warp items per case tile, between a minimum (32 rows, one index batch,
-  // for collect; 16 for distribute, whose rows carry less work) and 512: a
-  // small layer is latency-bound and finishes sooner in short items, a big
-  // one amortises each item's set-up over long ones.
-  P.rows_per_cta = opts.rows_per_cta > 0 ? opts.rows_per_cta : 0;
-  auto layer_rows = [&](int64_t total, bool distribute) -> int64_t {
-    if (opts.rows_per_cta > 0) return std::max<int64_t>(1, opts.rows_per_cta / NW);
-    int64_t items = opts.items_per_tile > 0 ? opts.items_per_tile : 192;
-    if (distribute && opts.items_per_tile_distribute > 0) items = opts.items_per_tile_distribute;
-    int64_t r = distribute ? 16 : 32;
-    while (r < 512 && r * 2 * items <= total) r *= 2;
-    return r;
-  };
-  P.citems.clear();
-  P.ditems.clear();
-  P.n_groups = 0;
-  P.n_partials = 0;
-  // one item per warp: whole segments when a segment fits the warp's rows,
-  // else the segment is split into pieces combined in piece order
-  auto emit = [&](std::vector<DItem> &out, int task, int64_t nseg, int64_t rows, int64_t ROWS) {
-    if (rows <= ROWS) {
-      int64_t per = std::max<int64_t>(1, ROWS / rows);
-      for (int64_t t0 = 0; t0 < nseg; t0 += per) {
-        DItem it{};
-        it.t0 = t0;
-        it.nt = std::min(per, nseg - t0);
-        it.u0 = 0;
-        it.nu = rows;
-        it.task = task;
-        it.split = 0;
-        it.npieces = 1;
-        it.piece = 0;
-        it.group = -1;
-        it.partial = -1;
-        out.push_back(it);
-      }
-    } else {
-      int64_t np = (rows + ROWS - 1) / ROWS;
-      int64_t per = (rows + np - 1) / np;
-      np = (rows + per - 1) / per;
-      for (int64_t s = 0; s < nseg; ++s) {
-        int32_t group = -1, first = -1;
-        if (np > 1) {
-          group = (int32_t)P.n_groups++;
-          first = (int32_t)P.n_partials;
-          P.n_partials += np;
-        }
-        for (int64_t p = 0; p < np; ++p) {
-          DItem it{};
-          it.t0 = s;
-          it.nt = 1;
-          it.u0 = p * per;
-          it.nu = std::min(per, rows - p * per);
-          it.task = task;
-          it.split = 1;
-          it.npieces = (int32_t)np;
-          it.piece = (int32_t)p;
-          it.group = group;
-          it.partial = np > 1 ? first + (int32_t)p : -1;
-          out.push_back(it);
-        }
-      }
-    }
-  };
-  // Per size bucket (bucket b: 2^b <= rows < 2^(b+1)) the caller may fix
-  // the rows of a work item; jt_autotune times these per bucket.  A value
-  // is rounded down to a power of two in [16, 4096].
-  auto bucket_rows = [&](const int32_t *table, int64_t rows, int64_t layer_value) -> int64_t {
-    if (opts.rows_per_cta > 0) return layer_value;
-    const int b = size_bucket(rows);
-    if (table[b] <= 0) return layer_value;
-    int64_t r = 16;
-    while (r < 4096 && r * 2 <= table[b]) r *= 2;
-    return r;
-  };
-  P.c_bucket_rows.fill(0);
-  P.d_bucket_rows.fill(0);
-  P.c_bucket_entries.fill(0);
-  P.d_bucket_entries.fill(0);
-  P.levels.assign(P.height + 1, Level{});
-  for (int L = 0; L <= P.height; ++L) {
-    Level &lv = P.levels[L];
-    lv.c_item_begin = (int64_t)P.citems.size();
-    int64_t crows = 0, drows = 0;
-    for (int c = 0; c < m; ++c) {
-      if (P.cl[c].depth != L) continue;
-      crows += P.cl[c].size;
-      for (int t : tasks_of[c]) drows += P.dtask[t].T * P.dtask[t].U;
-    }
-    const int64_t cR = layer_rows(crows, false), dR = layer_rows(drows, true);
-    for (int c = 0; c < m; ++c) {
-      if (P.cl[c].depth != L) continue;
-      const int64_t r = bucket_rows(opts.collect_rows_by_bucket, P.cl[c].size, cR);
-      const int b = size_bucket(P.cl[c].size);
-      P.c_bucket_rows[b] = std::max<int32_t>(P.c_bucket_rows[b], (int32_t)r);
-      P.c_bucket_entries[b] += P.cl[c].size;
-      emit(P.citems, c, P.cl[c].nsep, P.cl[c].R, r);
-      lv.c_max_maps = std::max(lv.c_max_maps, P.dcl[c].sev_end - P.dcl[c].map_begin);
-    }
-    lv.c_item_end = (int64_t)P.citems.size();
-    lv.d_item_begin = (int64_t)P.ditems.size();
-    for (int c = 0; c < m; ++c) {
-      if (P.cl[c].depth != L) continue;
-      for (int t : tasks_of[c]) {
-        const int64_t rows = P.dtask[t].T * P.dtask[t].U;
-        const int64_t r = bucket_rows(opts.distribute_rows_by_bucket, rows, dR);
-        const int b = size_bucket(rows);
-        P.d_bucket_rows[b] = std::max<int32_t>(P.d_bucket_rows[b], (int32_t)r);
-        P.d_bucket_entries[b] += rows;
-        emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U, r);
-      }
-    }
-    lv.d_item_end = (int64_t)P.ditems.size();
-  }
-  // dataflow schedule: flow layers (collect deepest first, distribute from
-  // the root) and each clique's producers on its tile
-  P.c_flow_pref.assign(1, 0);
-  P.d_flow_pref.assign(1, 0);
-  P.c_flow_begin.clear();
-  P.d_flow_begin.clear();
-  for (int k = 0; k <= P.height; ++k) {
-    const Level &lc = P.levels[P.height - k];
-    P.c_flow_begin.push_back(lc.c_item_begin);
-    P.c_flow_pref.push_back(P.c_flow_pref.back() + (lc.c_item_end - lc.c_item_begin));
-    const Level &ld = P.levels[k];
-    P.d_flow_begin.push_back(ld.d_item_begin);
-    P.d_flow_pref.push_back(P.d_flow_pref.back() + (ld.d_item_end - ld.d_item_begin));
-  }
-  P.c_need.assign(m, 0);
-  P.d_need.assign(m, 0);
-  P.c_notify.assign(m, -1);
-  for (const DItem &it : P.citems) {
-    const HostClique &K = P.cl[it.task];
-    if (K.parent >= 0 && K.n_up > 0) {
-      P.c_notify[it.task] = K.parent;
-      ++P.c_need[K.parent];
-    }
-  }
-  for (const DItem &it : P.ditems) {
-    const DTask &T = P.dtask[it.task];
-    if (T.kind == TASK_CHILD) ++P.d_need[T.dst];
-  }
-  if (opts.stall_clique > 0) {
-    if (opts.stall_clique > m) {
-      err = "stall_clique out of range";
-      return JT_EINVAL;
-    }
-    ++P.c_need[opts.stall_clique - 1];  // a producer that never comes
-  }
+  st = emit_work(P, opts, err);
+  if (st != JT_OK) return st;
 
   P.base_exp_sum = 0;
   for (int c = 0; c < m; ++c) P.base_exp_sum += base_exp[c];

@@ -218,6 +218,10 @@ struct Plan {
 // compile.cpp
 jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
                      const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err);
+// the work lists of a built plan (items of both passes, flow layers,
+// producer counts) for the work-shape options of opts (items_per_tile*,
+// rows_per_cta, *_rows_by_bucket, stall_clique)
+jt_status emit_work(Plan &P, const jt_compile_opts &opts, std::string &err);
 // build_plan on the network pruned to opts.query_set (build_plan when none)
 jt_status build_plan_pruned(int32_t n, const int32_t *card, const int32_t *pptr, const int32_t *par,
                             const double *cpt, const jt_compile_opts &opts, Plan &P, std::string &err);

@@ -25,7 +25,8 @@ struct ArenaLayout {
 // the CUDA graphs captured against it (one per tile count).
 struct Arena {
   void *mem = nullptr;
-  size_t bytes = 0;
+  size_t bytes = 0;        // bytes of the current layout
+  size_t alloc_bytes = 0;  // bytes of the allocation (>= bytes)
   int tiles = 0;
   bool owns = true;
   DevArena da{};
@@ -53,6 +54,8 @@ struct jt_plan {
   cudaStream_t capture_stream = nullptr;  // private stream for graph capture
   void *d_static = nullptr;
   size_t static_bytes = 0;
+  void *d_work = nullptr;                 // work lists (items, flow tables), replaced by retile
+  size_t work_bytes = 0;
   int flow_collect_blocks = 0;            // dataflow grids: SMs x resident blocks per SM
   int flow_distribute_blocks = 0;
   jt::DevPlan dp{};
@@ -69,6 +72,10 @@ struct jt_plan {
 };
 
 namespace jt {
+// give a compiled plan the work shape of opts (items_per_tile*, rows_per_cta,
+// *_rows_by_bucket): new work lists uploaded, graphs dropped, the arena
+// rebound in place when the new layout fits it (else freed)
+jt_status retile(jt_plan *pl, const jt_compile_opts &opts);
 jt_status run_chunk(jt_plan *pl, Arena &a, const int32_t *d_ev, int32_t nc, double *d_lp, double *d_post,
                     int32_t *d_st, cudaStream_t s);
 // JT_ETIMEOUT (and the flag cleared) when a kernel reported an expired
