@@ -204,6 +204,75 @@ def aggregate_rate(cases_per_rank: int, world: int, ms_per_step: float) -> float
     return cases_per_rank * world / (ms_per_step / 1e3)
 
 
+class EventTimer:
+    """Device time of the timed region: CUDA events on the launching stream."""
+
+    def __init__(self, stream):
+        import torch
+        self.stream = stream
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+
+    def start(self):
+        self.e0.record(self.stream)
+
+    def stop(self):
+        self.e1.record(self.stream)
+
+    def ms(self):
+        return self.e0.elapsed_time(self.e1)
+
+
+class WallTimer:
+    """Host wall time (for ranks without a GPU)."""
+
+    def start(self):
+        self.t0 = time.perf_counter()
+
+    def stop(self):
+        self.t1 = time.perf_counter()
+
+    def ms(self):
+        return 1e3 * (self.t1 - self.t0)
+
+
+def timed_region(step, steps, dist, device, timer, sync=lambda: None):
+    """`steps` calls of step between a barrier and a synchronisation on both
+    sides; returns the slowest rank's milliseconds (every rank gets it)."""
+    if dist:
+        dist.barrier()
+    sync()
+    timer.start()
+    for _ in range(steps):
+        step()
+    timer.stop()
+    sync()
+    if dist:
+        dist.barrier()
+    return max_over_ranks(timer.ms(), dist, device)
+
+
+def base_line(value, world, steps, warmup, ms_per_step):
+    """The keys every line of this arm carries."""
+    return {"metric": METRIC, "value": value, "unit": "cases/s", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+
+
+def spawn_ranks(n):
+    """--gpus N outside torchrun: relaunch this command as N ranks on this
+    node, one GPU each (torch.distributed.run, rendezvous on 127.0.0.1);
+    rank 0 prints the line.  Returns the launcher's exit status."""
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.run(cmd).returncode
+
+
 def _oracle_rate(net, ev, threads, budget_s):
     """Oracle cases/s on up to len(ev) cases, stopping after ~budget_s."""
     import oracle  # CPU baseline leg only
@@ -222,12 +291,18 @@ def _oracle_rate(net, ev, threads, budget_s):
 SERVING_PLANS = ["bn60", "bn110", "bn420", "bn1000"]
 
 
+ROLLING_TILES = {"bn60": 16, "bn1000": 16, "bn110": 6, "bn420": 4}
+
+
 def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, max_batch: int = 64,
-                arena_gb: float = 48.0, schedule=None):
+                arena_gb: float = 48.0, schedule=None, min_requests: int = 20000, rolling: bool = False):
     """The serving mix: resident plans of the four networks, one-case requests
     on a uniformly chosen plan with 5-30 % observed, Poisson arrivals at
     fractions of the measured saturated rate.  Returns p50/p99 latency
-    (submit -> result on the host) and cases/s per offered rate."""
+    (submit -> result on the host) and cases/s per offered rate, overall and
+    per plan.  rolling: every plan is served with iteration-level batching
+    (resident tiles that advance one tree layer per tick; requests join at
+    the next tick) instead of batch slots."""
     import paper_2212_04241_gb300.jt as J
     from synth import configs
     from synth.bn import sample_cases
@@ -264,31 +339,59 @@ def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, 
 
     def fresh():
         srv = J.Server(arena_bytes=int(arena_gb * (1 << 30)), max_batch=max_batch, max_inflight=8)
-        return srv, [srv.add_plan(pl) for pl in plans]
+        if not rolling:
+            return srv, [srv.add_plan(pl) for pl in plans]
+        pids = [None] * len(plans)
+        for i in sorted(range(len(plans)), key=lambda j: -ROLLING_TILES[SERVING_PLANS[j]]):
+            for t in range(ROLLING_TILES[SERVING_PLANS[i]], 0, -1):   # as many tiles as the pool holds
+                try:
+                    pids[i] = srv.add_plan(plans[i], rolling_tiles=t)
+                    tiles_used[SERVING_PLANS[i]] = t
+                    break
+                except J.JTError:
+                    continue
+            if pids[i] is None:
+                raise RuntimeError(f"rolling plan {SERVING_PLANS[i]} does not fit the pool")
+        return srv, pids
+
+    tiles_used = {}
 
     srv, pids = fresh()
     drive(srv, pids, 2000, None)  # warm-up: slots, graphs
     n_sat = 20000
     sat = n_sat / drive(srv, pids, n_sat, None)
     srv.close()
-    out = {"plans": SERVING_PLANS, "max_batch": max_batch, "arena_gb": arena_gb,
-           "schedule": "layers" if sched == J.JT_SCHEDULE_LAYERS else "dataflow",
+    out = {"plans": SERVING_PLANS, "arena_gb": arena_gb,
+           "mode": "rolling tiles (iteration-level batching)" if rolling else "batch slots",
            "saturated_cases_per_s": sat, "rates": []}
+    if rolling:
+        out["tiles"] = dict(tiles_used)
+        out["tile_cases"] = {nm: int(pl.info()["tile_cases"]) for nm, pl in zip(SERVING_PLANS, plans)}
+    else:
+        out["max_batch"] = max_batch
+        out["schedule"] = "layers" if sched == J.JT_SCHEDULE_LAYERS else "dataflow"
     for f in rates:
         rate = f * sat
-        n_req = int(max(2000, min(200000, rate * duration_s)))
+        n_req = int(max(min_requests, min(200000, rate * duration_s)))
         srv, pids = fresh()
-        drive(srv, pids, 500, None)
-        srv.close()
-        srv, pids = fresh()
+        drive(srv, pids, 500, None)     # warm-up on this server: slots bound, graphs captured
+        srv.reset_latency()
+        st0 = srv.stats()
         dt = drive(srv, pids, n_req, rate)
         st = srv.stats()
+        per_plan = {}
+        for nm, pid in zip(SERVING_PLANS, pids):
+            ps = srv.plan_stats(pid)
+            per_plan[nm] = {"completed": ps["completed"], "p50_ms": ps["p50_ns"] / 1e6, "p99_ms": ps["p99_ns"] / 1e6}
         srv.close()
         out["rates"].append({"offered_fraction": f, "offered_cases_per_s": rate, "requests": n_req,
                              "achieved_cases_per_s": n_req / dt, "p50_ms": st["p50_ns"] / 1e6,
-                             "p99_ms": st["p99_ns"] / 1e6, "batches": st["batches"],
+                             "p99_ms": st["p99_ns"] / 1e6, "batches": st["batches"] - st0["batches"],
                              "largest_batch": st["largest_batch"],
-                             "peak_arena_gb": st["peak_arena_bytes"] / 2**30})
+                             "peak_arena_gb": st["peak_arena_bytes"] / 2**30,
+                             "slot_creations": st["slot_creations"] - st0["slot_creations"],
+                             "slot_evictions": st["slot_evictions"] - st0["slot_evictions"],
+                             "per_plan": per_plan})
     return out
 
 
@@ -353,6 +456,8 @@ def main():
     ap.add_argument("--serving-only", action="store_true", help="only the serving-mix measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return spawn_ranks(args.gpus)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -392,7 +497,8 @@ def main():
 
     import torch
     if args.serving_only:
-        print(json.dumps({"serving": run_serving()}), flush=True)
+        print(json.dumps({"serving": {"batch_slots": run_serving(), "rolling": run_serving(rolling=True)}}),
+              flush=True)
         return 0
     torch.cuda.set_device(local_rank)
     dist = None
@@ -447,20 +553,8 @@ def main():
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.5)  # let the sampler start before the timed region
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    ms = timed_region(step, args.steps, dist, "cuda", EventTimer(stream), torch.cuda.synchronize)
     clock_info = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_per_step = ms / args.steps
     value = aggregate_rate(n_cases, world, ms_per_step)
 
@@ -559,18 +653,14 @@ def main():
 
     serving = None
     if rank == 0 and not args.no_serving and world == 1:
-        serving = run_serving()
+        serving = {"batch_slots": run_serving(), "rolling": run_serving(rolling=True)}
 
     if dist:
         dist.destroy_process_group()
     if rank != 0:
         return 0
     launches = info["kernels_per_chunk"] * ((n_cases + info["chunk_cases"] - 1) // max(1, info["chunk_cases"]))
-    line = {
-        "metric": METRIC,
-        "value": value, "unit": "cases/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+    line = dict(base_line(value, world, args.steps, args.warmup, ms_per_step), **{
         "config": {"workload": WORKLOADS[name] + (f"_observedset{args.observed_set}" if observed_set else "")
                    + (f"_queryset{args.query_set}" if query_set else ""),
                    "observed_set": observed_set, "query_set": query_set, "pruned_vars": info["pruned_vars"], "cases_per_gpu": n_cases, "tile_cases": info["tile_cases"],
@@ -589,7 +679,7 @@ def main():
         "gpu_launches": int(launches * args.steps),
         "roofline": roofline, "clocks": clock_info, "e2e": e2e, "plain_gpu": plain,
         "cpu_baseline": cpu, "cpu_layer_parallel": cpu_layers, "accuracy": accuracy, "serving": serving,
-    }
+    })
     print(json.dumps(line), flush=True)
     return 0
 

@@ -206,6 +206,14 @@ typedef struct {
   int32_t distribute_rows_by_bucket[JT_SIZE_BUCKETS];
                               /* the same for the distribute pass, bucketed
                                  by each task's source rows */
+  int32_t fuse_distribute;    /* 1 (default): two marginalisations of the
+                                 same clique table in the distribute pass
+                                 (two child separators, or a separator and
+                                 a posterior variable) share one read of
+                                 the table when the second one's targets
+                                 per block of common variables fit a warp's
+                                 shared-memory sums; 0: every marginal reads
+                                 the table on its own */
 } jt_compile_opts;
 
 typedef struct {
@@ -379,7 +387,7 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
  * between threads that Section 2 attributes to tables of very different
  * sizes).  Times the collect and the distribute launches of n_cases cases
  * separately on the current device (jt_profile: one warm-up run, then the
- * best of two) in base's schedule, in two stages:
+ * best of two) in base's schedule, in three stages:
  *   1. per tile width (cases per thread 4 and 8, unless base fixes it) the
  *      work-item target of each pass over {96, 192, 384, 768, 1536} items
  *      per tile and layer; the fastest width and targets are kept;
@@ -388,8 +396,11 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
  *      of one warp work item -- hence the warps (threads) per table and
  *      the tile shape rows x cases -- over the powers of two 32 .. 4096,
  *      each pass keeping its own best value (coordinate descent; a change
- *      is kept when it is at least 1 % faster).
- * Between candidates only the work lists are rebuilt, not the plan.
+ *      is kept when it is at least 1 % faster);
+ *   3. the result with fuse_distribute turned the other way (recompiled),
+ *      kept if it is at least 1 % faster.
+ * Between the candidates of stages 1 and 2 only the work lists are
+ * rebuilt, not the plan.
  * Writes the result to *best (base fields kept; the bucket tables in
  * collect_rows_by_bucket / distribute_rows_by_bucket) and its pass time per
  * case in ns to *best_ns_per_case (may be NULL).  base may be NULL for the
@@ -435,16 +446,40 @@ JT_API const char *jt_last_error(void);
  * Serving: a continuous-batching request loop (one host thread) over
  * resident plans.  Requests are single evidence cases; the loop coalesces
  * pending requests of the same plan into batches, admits a batch when its
- * arena bytes fit the server's budget (arena_bytes; 0 = 16 GiB), keeps up to
- * max_inflight batches in flight on separate CUDA streams so that batches
- * of different plans overlap on the device, and hands results back by
- * ticket.  A request's result does not depend on which other requests
- * share its batch (fixed per-case reduction order).
+ * per-batch tables fit the server's device pool (arena_bytes; 0 = 16 GiB),
+ * keeps up to max_inflight batches in flight on separate CUDA streams so
+ * that batches of different plans overlap on the device, and hands results
+ * back by ticket.  A request's result does not depend on which other
+ * requests share its batch (fixed per-case reduction order).
+ * jt_server_create allocates the pool (one device allocation of
+ * arena_bytes, JT_ENOMEM if it fails) and the streams; jt_server_add_plan
+ * allocates the plan's pinned host and device staging buffers (outside the
+ * pool); the request loop itself allocates nothing: a plan's batch slot is
+ * a region of the pool, reused batch after batch, and idle slots of other
+ * plans are evicted (least recently used first) when the pool is full.
  */
 JT_API jt_status jt_server_create(int64_t arena_bytes, int32_t max_batch, int32_t max_inflight,
                            jt_server **out);
 /* Register a plan (not copied; it must outlive the server). */
 JT_API jt_status jt_server_add_plan(jt_server *srv, jt_plan *plan, int32_t *plan_id);
+/*
+ * Register a plan served with iteration-level batching (no counterpart in
+ * the paper; the layer-by-layer order of Section 2 applied across
+ * requests): the plan's tables for `tiles` case tiles (jt_plan_info
+ * tile_cases cases each) are carved out of the server's pool now and stay
+ * resident.  Each tile takes up to tile_cases pending requests and advances
+ * one tree layer per tick -- collect layers from the deepest to the root,
+ * then distribute layers from the root, then its log P(e) and posterior
+ * kernels -- and one tick is two launches over every active tile, each at
+ * its own layer.  A request arriving while other tiles are mid-pass starts
+ * at the next tick, in a free tile, instead of waiting for a whole pass.
+ * At most two ticks of a plan are in flight.  Results are the same bit for
+ * bit as the batch-slot path's (same kernels per tile, fixed per-case
+ * reduction order).  Allocates the plan's staging buffers and stream.
+ * JT_ENOMEM when the tiles do not fit the free part of the pool.  The plan
+ * must not be given a new work shape while the server holds it.
+ */
+JT_API jt_status jt_server_add_plan_rolling(jt_server *srv, jt_plan *plan, int32_t tiles, int32_t *plan_id);
 /*
  * Queue one case.  evidence: int32 [n_vars of the plan]; query_vars: the
  * variables whose posteriors the caller wants (n_query entries, or NULL and
@@ -463,12 +498,25 @@ JT_API jt_status jt_poll(jt_server *srv, uint64_t ticket, double *log_pe, double
 /* Block until every submitted request has completed. */
 JT_API jt_status jt_server_drain(jt_server *srv);
 /*
- * Counters: out[0] completed requests, out[1] batches launched, out[2]
- * largest batch, out[3] peak arena bytes in use, out[4] p50 latency (ns),
- * out[5] p99 latency (ns), out[6] requests pending.  Latency is submit ->
- * result ready on the host.
+ * Counters (out holds 9 entries): out[0] completed requests, out[1] batches
+ * launched, out[2] largest batch, out[3] peak pool bytes in use, out[4] p50
+ * latency (ns), out[5] p99 latency (ns), out[6] requests pending or in
+ * flight, out[7] batch slots created (regions of the pool bound to a plan),
+ * out[8] slots evicted to make room for another plan's.  Latency is
+ * submit -> result ready on the host.
  */
 JT_API jt_status jt_server_stats(jt_server *srv, int64_t *out);
+/*
+ * Counters of one plan (out holds 4 entries): out[0] completed requests,
+ * out[1] batches launched, out[2] p50 latency (ns), out[3] p99 latency
+ * (ns).  JT_ENOTFOUND for an unknown plan id.
+ */
+JT_API jt_status jt_server_plan_stats(jt_server *srv, int32_t plan_id, int64_t *out);
+/*
+ * Forget the latency samples collected so far (for every plan), e.g. after
+ * a warm-up; the counters and the resident slots are kept.
+ */
+JT_API jt_status jt_server_reset_latency(jt_server *srv);
 JT_API void jt_server_destroy(jt_server *srv);
 
 #ifdef __cplusplus

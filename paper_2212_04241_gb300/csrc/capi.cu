@@ -260,6 +260,7 @@ extern "C" void jt_default_opts(jt_compile_opts *o) {
   o->arena_bytes = 0;
   o->use_graphs = 1;
   o->rescale = 1;
+  o->fuse_distribute = 1;
 }
 
 template <class T>
@@ -300,6 +301,13 @@ static jt_status upload_work(jt_plan *pl) {
   D.d_need = reinterpret_cast<const uint32_t *>(b + o_dn);
   D.n_partials = std::max<int64_t>(1, P.n_partials);
   D.n_groups = std::max<int64_t>(1, P.n_groups);
+  D.fused_items = 0;
+  for (const DItem &it : P.ditems) D.fused_items += it.fused;
+  // the distribute grid fills the GPU once at its kernel's occupancy
+  int sms = 0;
+  JT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
+  pl->flow_distribute_blocks =
+      sms * flow_blocks_per_sm(P.cpt_per_thread, false, false, 0, D.fused_items > 0 ? P.sec_rows : 0);
   return JT_OK;
 }
 
@@ -361,6 +369,7 @@ static jt_status upload_plan(jt_plan *pl) {
   D.io_n = P.io_n;
   D.n_dropped = (int32_t)P.io_dropped.size();
   D.n_nan_cols = (int32_t)P.io_nan_cols.size();
+  D.sec_rows = P.sec_rows;
   jt_status wst = upload_work(pl);
   if (wst != JT_OK) return wst;
   D.n_flow_layers = P.height + 1;
@@ -392,7 +401,7 @@ static jt_status upload_plan(jt_plan *pl) {
   int sms = 0;
   JT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
   pl->flow_collect_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, true, P.n_sliced > 0, max_maps);
-  pl->flow_distribute_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, false, false, 0);
+  JT_CUDA_TRY(configure_distribute_smem(P.cpt_per_thread, distribute_smem_bytes(P.cpt_per_thread, P.sec_rows)));
   return JT_OK;
 }
 
@@ -1112,6 +1121,23 @@ static jt_status jt_autotune_impl(int32_t n_vars, const int32_t *card, const int
     }
     if (pl) jt_plan_free(pl);
     if (st != JT_OK) result = st;
+  }
+  // stage 3: the tuned shape with fused distribute pairs turned the other
+  // way (fused items need the distribute kernel that runs at fewer blocks
+  // per SM; which one wins depends on the network)
+  if (result == JT_OK && best_cw > 0) {
+    jt_compile_opts alt = best_o;
+    alt.fuse_distribute = best_o.fuse_distribute ? 0 : 1;
+    jt_plan *pl = nullptr;
+    jt_status st = jt_compile(n_vars, card, parent_ptr, parents, cpt, &alt, &pl);
+    double c_ms = -1, d_ms = -1;
+    if (st == JT_OK) st = time_plan(pl, c_ms, d_ms);
+    if (pl) jt_plan_free(pl);
+    if (st != JT_OK) result = st;
+    else if (c_ms + d_ms < 0.99 * best_total) {
+      best_o = alt;
+      best_total = c_ms + d_ms;
+    }
   }
   cudaFree(d_ev);
   cudaFree(d_lp);

@@ -359,6 +359,58 @@ jt_status emit_work(Plan &P, const jt_compile_opts &opts, std::string &err) {
   P.d_bucket_rows.fill(0);
   P.c_bucket_entries.fill(0);
   P.d_bucket_entries.fill(0);
+  // A fused task's items hold whole primary targets inside one F-block, or
+  // whole F-blocks; an F-block larger than an item, or whose secondary
+  // targets would sum more than kFusedTerms rows, is cut into pieces that
+  // write their secondary sums as partials, which the last piece to finish
+  // adds in piece order.
+  auto emit_fused = [&](int task, int64_t ROWS) {
+    const DTask &T = P.dtask[task];
+    const int64_t a = T.sec_a, b = T.sec_b, U = T.U, nF = T.T / a, Q = U / b;
+    const int64_t R2 = ROWS;
+    int64_t tp = std::max<int64_t>(1, std::min<int64_t>(R2 / U, kFusedTerms / Q));
+    if (tp >= a) {
+      const int64_t per = std::max<int64_t>(1, R2 / (a * U));
+      for (int64_t f0 = 0; f0 < nF; f0 += per) {
+        DItem it{};
+        it.t0 = f0 * a;
+        it.nt = std::min(per, nF - f0) * a;
+        it.u0 = 0;
+        it.nu = U;
+        it.task = task;
+        it.split = 0;
+        it.npieces = 1;
+        it.group = -1;
+        it.partial = -1;
+        it.fused = 1;
+        P.ditems.push_back(it);
+      }
+      return;
+    }
+    int64_t np = (a + tp - 1) / tp;
+    tp = (a + np - 1) / np;
+    np = (a + tp - 1) / tp;
+    for (int64_t f = 0; f < nF; ++f) {
+      const int32_t group = (int32_t)P.n_groups++;
+      const int32_t first = (int32_t)P.n_partials;
+      P.n_partials += np * b;
+      for (int64_t p = 0; p < np; ++p) {
+        DItem it{};
+        it.t0 = f * a + p * tp;
+        it.nt = std::min(tp, a - p * tp);
+        it.u0 = 0;
+        it.nu = U;
+        it.task = task;
+        it.split = 0;
+        it.npieces = (int32_t)np;
+        it.piece = (int32_t)p;
+        it.group = group;
+        it.partial = first + (int32_t)(p * b);
+        it.fused = 1;
+        P.ditems.push_back(it);
+      }
+    }
+  };
   P.levels.assign(P.height + 1, Level{});
   for (int L = 0; L <= P.height; ++L) {
     Level &lv = P.levels[L];
@@ -383,13 +435,25 @@ jt_status emit_work(Plan &P, const jt_compile_opts &opts, std::string &err) {
     lv.d_item_begin = (int64_t)P.ditems.size();
     for (int c = 0; c < m; ++c) {
       if (P.cl[c].depth != L) continue;
+      // a pair is fused where its items are long enough for the partial
+      // sums of F-block pieces to cost little; elsewhere both tasks get
+      // plain items
       for (int t : tasks_of[c]) {
+        DTask &T = P.dtask[t];
+        if (T.sec_b > 0) {
+          const int64_t r = bucket_rows(opts.distribute_rows_by_bucket, T.T * T.U, dR);
+          P.dtask[T.sec_task].absorbed = r >= kFusedMinRows ? 1 : 0;
+        }
+      }
+      for (int t : tasks_of[c]) {
+        if (P.dtask[t].absorbed) continue;  // computed by its fused partner's items
         const int64_t rows = P.dtask[t].T * P.dtask[t].U;
         const int64_t r = bucket_rows(opts.distribute_rows_by_bucket, rows, dR);
         const int b = size_bucket(rows);
         P.d_bucket_rows[b] = std::max<int32_t>(P.d_bucket_rows[b], (int32_t)r);
         P.d_bucket_entries[b] += rows;
-        emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U, r);
+        if (P.dtask[t].sec_b > 0 && P.dtask[P.dtask[t].sec_task].absorbed) emit_fused(t, r);
+        else emit(P.ditems, t, P.dtask[t].T, P.dtask[t].U, r);
       }
     }
     lv.d_item_end = (int64_t)P.ditems.size();
@@ -421,6 +485,7 @@ jt_status emit_work(Plan &P, const jt_compile_opts &opts, std::string &err) {
   for (const DItem &it : P.ditems) {
     const DTask &T = P.dtask[it.task];
     if (T.kind == TASK_CHILD) ++P.d_need[T.dst];
+    if (it.fused && T.sec_kind == TASK_CHILD) ++P.d_need[T.sec_dst];
   }
   if (opts.stall_clique > 0) {
     if (opts.stall_clique > m) {
@@ -866,6 +931,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   P.tile = 32 * P.cpt_per_thread;
   // distribute tasks: children first (ascending), then owned posteriors
   std::vector<std::vector<int>> tasks_of(m);
+  std::vector<std::vector<int>> task_vars;  // target variables of each task
   for (int c = 0; c < m; ++c) {
     const HostClique &C = P.cl[c];
     auto make_task = [&](const std::vector<int> &target, int kind, int dst, int64_t dst_row, bool from_sep = false) {
@@ -905,8 +971,11 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
       t.dst = dst;
       t.dst_row = dst_row;
       t.src_sep = from_sep ? 1 : 0;
+      t.op_off = -1;
+      t.sec_task = -1;
       tasks_of[c].push_back((int)P.dtask.size());
       P.dtask.push_back(t);
+      task_vars.push_back(target);
     };
     for (int ch : C.children) {
       const HostClique &K = P.cl[ch];
@@ -916,6 +985,110 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     }
     for (int v : C.owned) make_task(std::vector<int>{v}, TASK_POSTERIOR, v, P.post_off[v]);
     for (int v : C.owned_sep) make_task(std::vector<int>{v}, TASK_POSTERIOR, v, P.post_off[v], true);
+  }
+
+  // Fused pairs: two tasks reading the same clique table share one pass
+  // over it (see DTask).  The secondary's per-F-block sums live in shared
+  // memory, kFusedRowBytes per warp at most, so its targets per F-block
+  // are bounded by that over the tile's row bytes.
+  P.sec_rows = 0;
+  if (opts.fuse_distribute) {
+    const int64_t bmax = kFusedRowBytes / (4 * (int64_t)P.tile);
+    for (int c = 0; c < m; ++c) {
+      const HostClique &C = P.cl[c];
+      std::vector<int> cand;
+      for (int t : tasks_of[c])
+        if (!P.dtask[t].src_sep) cand.push_back(t);
+      auto in = [](const std::vector<int> &vs, int v) { return std::find(vs.begin(), vs.end(), v) != vs.end(); };
+      auto card_of = [&](const std::vector<int> &vs) {
+        int64_t r = 1;
+        for (int v : vs) r *= card[v];
+        return r;
+      };
+      while (cand.size() >= 2) {
+        // the pair whose secondary needs the fewest shared-memory rows
+        int bi = -1, bj = -1;
+        int64_t best_b = 0;
+        for (int i : cand)
+          for (int j : cand) {
+            if (i == j) continue;
+            const std::vector<int> &Ti = task_vars[i], &Tj = task_vars[j];
+            std::vector<int> only_j;
+            for (int v : Tj)
+              if (!in(Ti, v)) only_j.push_back(v);
+            const int64_t b = card_of(only_j);
+            if (b > bmax || P.dtask[i].U > kFusedMaxRows) continue;
+            if (bi < 0 || b < best_b) { bi = i; bj = j; best_b = b; }
+          }
+        if (bi < 0) break;
+        const std::vector<int> &Ti = task_vars[bi], &Tj = task_vars[bj];
+        // layout-ordered variable lists: F, T1 \ F, (T2 \ T1), the rest
+        std::vector<int> fpos, tpos, kpos, rpos;
+        for (int i = 0; i < (int)C.vars.size(); ++i) {
+          const int v = C.vars[i];
+          const bool a1 = in(Ti, v), a2 = in(Tj, v);
+          (a1 && a2 ? fpos : a1 ? tpos : a2 ? kpos : rpos).push_back(i);
+        }
+        auto cards_at = [&](const std::vector<int> &pos) {
+          std::vector<int> r;
+          for (int i : pos) r.push_back(C.card[i]);
+          return r;
+        };
+        // row-major stride of clique position i inside the enumeration of a
+        // target's variables taken in layout order
+        auto target_stride = [&](const std::vector<int> &tv, int i) -> int64_t {
+          int64_t s2 = 1;
+          for (int q = (int)C.vars.size() - 1; q >= 0; --q) {
+            if (!in(tv, C.vars[q])) continue;
+            if (q == i) return s2;
+            s2 *= C.card[q];
+          }
+          return 0;
+        };
+        std::vector<int> tord = fpos;  // primary targets: F outermost
+        tord.insert(tord.end(), tpos.begin(), tpos.end());
+        std::vector<int> uord = kpos;  // rows: the secondary's own variables outermost
+        uord.insert(uord.end(), rpos.begin(), rpos.end());
+        std::vector<int64_t> wa, wsa, wop, wb, wsb, wku;
+        for (int i : tord) {
+          wa.push_back(C.stride[i]);
+          wsa.push_back(i < C.n_up ? C.stride[i] / C.R : 0);
+          wop.push_back(target_stride(Ti, i));
+        }
+        int64_t ks = 1;
+        std::vector<int64_t> kstride(kpos.size());
+        for (int q = (int)kpos.size() - 1; q >= 0; --q) { kstride[q] = ks; ks *= C.card[kpos[q]]; }
+        for (size_t q = 0; q < uord.size(); ++q) {
+          const int i = uord[q];
+          wb.push_back(C.stride[i]);
+          wsb.push_back(i < C.n_up ? C.stride[i] / C.R : 0);
+          wku.push_back(q < kpos.size() ? kstride[q] : 0);
+        }
+        std::vector<int64_t> wosf, wosk;
+        for (int i : fpos) wosf.push_back(target_stride(Tj, i));
+        for (int i : kpos) wosk.push_back(target_stride(Tj, i));
+        DTask &T = P.dtask[bi];
+        const DTask &S = P.dtask[bj];
+        T.fA_off = table_or_zero(cards_at(tord), wa);
+        T.fsA_off = table_or_zero(cards_at(tord), wsa);
+        T.op_off = table_or_zero(cards_at(tord), wop);
+        T.fB_off = table_or_zero(cards_at(uord), wb);
+        T.fsB_off = table_or_zero(cards_at(uord), wsb);
+        T.ku_off = table_or_zero(cards_at(uord), wku);
+        T.osf_off = table_or_zero(cards_at(fpos), wosf);
+        T.osk_off = table_or_zero(cards_at(kpos), wosk);
+        T.sec_a = (int32_t)card_of([&] { std::vector<int> r; for (int i : tpos) r.push_back(C.vars[i]); return r; }());
+        T.sec_b = (int32_t)best_b;
+        T.sec_kind = S.kind;
+        T.sec_dst = S.dst;
+        T.sec_dst_row = S.dst_row;
+        T.sec_task = bj;
+        P.dtask[bj].absorbed = 1;
+        P.sec_rows = std::max<int>(P.sec_rows, (int)best_b);
+        cand.erase(std::find(cand.begin(), cand.end(), bi));
+        cand.erase(std::find(cand.begin(), cand.end(), bj));
+      }
+    }
   }
 
   st = emit_work(P, opts, err);

@@ -67,7 +67,25 @@ struct DMap {
 //   product is that separator's calibrated marginal; sA = A, sB = B).
 //   kind TASK_CHILD: writes rho_child[t] = value(t) / phistar_child[t]
 //   kind TASK_POSTERIOR: writes the unnormalised marginal of variable dst
+//
+// Fused pair (sec_b > 0): the task also computes a second marginal of the
+// same table (the "secondary", another child separator or posterior
+// variable T2 of the clique) from the same rows, so the table is read once
+// for both.  With F = T1 and T2's common variables, the primary's targets
+// are enumerated F-block by F-block (t = f * sec_a + t', f over F's
+// entries, t' over T1 \ F's), and the rows u of a target with T2 \ T1's
+// variables outermost.  Within one F-block (sec_a consecutive targets) the
+// rows touch exactly sec_b secondary targets, k = Ku[u]; the warp sums
+// them in shared memory and writes target (f, k) at row
+// sec_dst_row + OSf[f] + OSk[k] (the secondary's own enumeration) when the
+// F-block ends.  The primary's target t is written at row
+// dst_row + OP[t] (its enumeration before the reordering).  The secondary
+// task itself is marked absorbed and gets no work items.
 enum { TASK_CHILD = 0, TASK_POSTERIOR = 1 };
+constexpr int64_t kFusedRowBytes = 6144;  // shared memory per warp for a fused pair's secondary sums
+constexpr int64_t kFusedMaxRows = 4096;   // a fused primary target has at most this many rows
+constexpr int64_t kFusedTerms = 256;      // rows summed per secondary target before a partial is written
+constexpr int64_t kFusedMinRows = 128;    // a pair is fused only where items hold at least this many rows
 struct DTask {
   int64_t T, U;
   int64_t A_off, B_off, sA_off, sB_off;  // int32 pool offsets
@@ -76,6 +94,21 @@ struct DTask {
   int32_t kind;
   int32_t dst;        // child clique / variable
   int32_t src_sep;
+  // fused pair (sec_b == 0: none); the fused items use their own tables
+  // (the fields above stay the task's plain enumeration, used when a work
+  // shape gives the pair plain items)
+  int64_t fA_off, fB_off, fsA_off, fsB_off;  // A, B, sA, sB of the reordered enumeration
+  int64_t op_off;     // OP[t]: primary target t's row offset (int32 pool; -1: t itself)
+  int64_t ku_off;     // Ku[u]: secondary target of row u inside the F-block
+  int64_t osf_off;    // OSf[f]
+  int64_t osk_off;    // OSk[k]
+  int64_t sec_dst_row;
+  int32_t sec_a;      // primary targets per F-block
+  int32_t sec_b;      // secondary targets per F-block
+  int32_t sec_kind;   // TASK_CHILD / TASK_POSTERIOR
+  int32_t sec_dst;    // child clique / variable
+  int32_t sec_task;   // index of the partner task
+  int32_t absorbed;   // 1: the partner of a fused pair (gets no items while the pair is fused)
 };
 
 // One warp's work item in a layer launch (the same list serves every tile).
@@ -92,6 +125,7 @@ struct DItem {
   int32_t piece;
   int32_t group;      // split group (counter index), -1 if npieces == 1
   int32_t partial;    // partial-sum slot of this piece
+  int32_t fused;      // 1: a fused pair's item (the task's primary and secondary marginals)
 };
 
 // Plain FP64 path: descriptor of a mixed-radix mapping from the entries of a
@@ -211,6 +245,7 @@ struct Plan {
 
   jt_compile_opts opts{};
   int cpt_per_thread = 4;
+  int sec_rows = 0;               // largest sec_b of the fused tasks (shared-memory rows per warp)
   int tile = 128;
   int rows_per_cta = 2048;
 };

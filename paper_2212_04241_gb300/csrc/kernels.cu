@@ -44,11 +44,18 @@ template <int CPT>
 constexpr int kCollectGroup = CPT >= 8 ? 2 : 4;
 template <int CPT>
 constexpr int kDistGroup = CPT >= 8 ? 2 : 4;
+// rows per group of the fused distribute item (its kernel runs at three
+// blocks per SM, with the registers for four rows)
+template <int CPT>
+constexpr int kFusedGroup = CPT >= 8 ? 2 : 4;
 // Resident blocks per SM the register allocation aims at: the collect
 // kernel keeps its row group in registers without spilling at 2; the
 // distribute kernel streams psi and gains from more warps in flight.
 constexpr int kCollectBlocksPerSM = 2;
 constexpr int kDistributeBlocksPerSM = 4;
+// the distribute kernels of plans with fused pairs carry both item kinds
+// and need more registers: three blocks per SM
+constexpr int kFusedBlocksPerSM = 3;
 
 // CPT cases of one thread inside a row of W = 32*CPT cases.  For CPT >= 4
 // the thread holds CPT/4 float4 pieces, piece v at columns 128*v + 4*lane;
@@ -615,13 +622,210 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
   }
 }
 
-template <int CPT>
-__global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute(DevPlan P, DevArena A, int64_t item_begin,
-                                                             int64_t n_items) {
+// One fused distribute work item (see DTask): whole primary targets
+// [t0, t0 + nt) of one F-block, or whole F-blocks.  Every row is read once:
+// the primary target's sum runs in registers (as in distribute_item), the
+// secondary targets of the F-block are summed in this warp's shared memory
+// (sec_b rows of W floats, each lane its own CPT columns, so no two lanes
+// touch the same word) and written when the F-block ends -- or, for a
+// piece of an F-block, written as partial sums that the last piece to
+// finish adds in piece order.
+template <int CPT, LoadMode RHO>
+__device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
+                                                      int lane, float *sec) {
+  constexpr int W = 32 * CPT;
+  constexpr int G = kFusedGroup<CPT>;
+  const DTask &T = P.tasks[it.task];
+  const DClique C = P.cl[T.clique];
+  const float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
+  const float *rho = A.rho + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
+  const bool root = C.is_root != 0;
+  Vec<CPT> rs;
+#pragma unroll
+  for (int k = 0; k < CPT; ++k)
+    rs.x[k] = root && P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + col_of<CPT>(lane, k)]))
+                   : 1.f;
+  const int32_t *__restrict__ At = P.ipool + T.fA_off;
+  const int32_t *__restrict__ sAt = P.ipool + T.fsA_off;
+  const int32_t *__restrict__ Bt = P.ipool + T.fB_off;
+  const int32_t *__restrict__ sBt = P.ipool + T.fsB_off;
+  const int32_t *__restrict__ Ku = P.ipool + T.ku_off;
+  const int32_t U = (int32_t)T.U, a = T.sec_a, nb2 = T.sec_b;
+
+  // a target's value: a separator ratio (0/0 := 0) or a posterior marginal
+  auto write = [&](int kind, int64_t row, const Vec<CPT> &val) {
+    if (kind == TASK_CHILD) {
+      const int64_t o = ((int64_t)tile * P.sep_rows + row) * W;
+      const Vec<CPT> ph = ldrow<CPT>(A.phistar + o, lane);
+      Vec<CPT> q;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) q.x[k] = (ph.x[k] > 0.f) ? val.x[k] / ph.x[k] : 0.f;
+      strow<CPT>(A.rho + o, lane, q);
+    } else {
+      strow<CPT>(A.post + ((int64_t)tile * P.post_rows + row) * W, lane, val);
+    }
+  };
+  auto sec_row = [&](int64_t f, int k) {
+    const DTask &Tt = P.tasks[it.task];
+    return Tt.sec_dst_row + __ldg(P.ipool + Tt.osf_off + f) + __ldg(P.ipool + Tt.osk_off + k);
+  };
+  for (int k = 0; k < nb2; ++k) strow<CPT>(sec + (int64_t)k * W, lane, vzero<CPT>());
+  // the secondary targets of F-block fb from shared memory (zeroed for the
+  // next F-block); a separator ratio needs phi*, so the divisors of two
+  // targets are requested together
+  auto flush_sec = [&](int64_t fb) {
+    const DTask &Tt = P.tasks[it.task];
+    for (int k0 = 0; k0 < nb2; k0 += 2) {
+      const int nk = min(2, nb2 - k0);
+      int64_t row[2];
+      Vec<CPT> val[2], ph[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        row[j] = j < nk ? sec_row(fb, k0 + j) : 0;
+        val[j] = ldrow<CPT>(sec + (int64_t)(k0 + min(j, nk - 1)) * W, lane);
+        if (Tt.sec_kind == TASK_CHILD && j < nk) ph[j] = ldrow<CPT>(A.phistar + ((int64_t)tile * P.sep_rows + row[j]) * W, lane);
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (j >= nk) break;
+        if (Tt.sec_kind == TASK_CHILD) {
+          Vec<CPT> q;
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) q.x[c] = (ph[j].x[c] > 0.f) ? val[j].x[c] / ph[j].x[c] : 0.f;  // 0/0 := 0
+          strow<CPT>(A.rho + ((int64_t)tile * P.sep_rows + row[j]) * W, lane, q);
+        } else {
+          strow<CPT>(A.post + ((int64_t)tile * P.post_rows + row[j]) * W, lane, val[j]);
+        }
+        strow<CPT>(sec + (int64_t)(k0 + j) * W, lane, vzero<CPT>());
+      }
+    }
+  };
+
+  const int32_t t_first = (int32_t)it.t0;
+  const int32_t count = (int32_t)(it.nt * (int64_t)U);
+  Vec<CPT> acc = vzero<CPT>(), comp = vzero<CPT>(), part = vzero<CPT>();
+  for (int32_t b0 = 0; b0 < count; b0 += 32) {
+    const int nb = min(32, count - b0);
+    const int32_t f = b0 + min(lane, nb - 1);
+    const int32_t tj = t_first + f / U, uj = f - (f / U) * U;
+    const int32_t ej = __ldg(At + tj) + __ldg(Bt + uj);
+    const int32_t xj = root ? 0 : __ldg(sAt + tj) + __ldg(sBt + uj);
+    const int32_t kj = __ldg(Ku + uj);
+    const unsigned last = __ballot_sync(kFull, uj == U - 1 && lane < nb);
+    const unsigned fend = __ballot_sync(kFull, uj == U - 1 && (tj % a) == a - 1 && lane < nb) &
+                          (it.npieces == 1 ? kFull : 0u);
+    // the batch's second group into L2 (the loop requests two groups ahead)
+    if (G < nb) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const float *pa = psi + (int64_t)__shfl_sync(kFull, ej, min(G + g, nb - 1)) * W + lane * CPT;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+      }
+    }
+    for (int r = 0; r < nb; r += G) {
+      Vec<CPT> p[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        p[g] = ldrow<CPT, LD_STREAM>(psi + (int64_t)__shfl_sync(kFull, ej, min(r + g, nb - 1)) * W, lane);
+      // rows two groups ahead are requested into L2 now (the group is half
+      // the plain item's, for registers; the prefetch keeps the bytes in flight)
+      if (r + 2 * G < nb) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const float *pa = psi + (int64_t)__shfl_sync(kFull, ej, min(r + 2 * G + g, nb - 1)) * W + lane * CPT;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+        }
+      }
+      if (!root) {
+        Vec<CPT> q[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          q[g] = ldrow<CPT, RHO>(rho + (int64_t)__shfl_sync(kFull, xj, min(r + g, nb - 1)) * W, lane);
+#pragma unroll
+        for (int g = 0; g < G; ++g) vmul<CPT>(p[g], q[g]);
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) vmul<CPT>(p[g], rs);
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        if (r + g < nb) {
+          // the secondary target of this row, summed in shared memory
+          float *srow = sec + (int64_t)__shfl_sync(kFull, kj, r + g) * W;
+          Vec<CPT> sv = ldrow<CPT>(srow, lane);
+          vadd<CPT>(sv, p[g]);
+          strow<CPT>(srow, lane, sv);
+          vadd<CPT>(part, p[g]);
+          if ((last >> (r + g)) & 1u) {  // primary target complete
+            kahan_fold<CPT>(acc, comp, part);
+            const int32_t t = __shfl_sync(kFull, tj, r + g);
+            const DTask &Tt = P.tasks[it.task];
+            write(Tt.kind, Tt.dst_row + __ldg(P.ipool + Tt.op_off + t), acc);
+            acc = vzero<CPT>();
+            comp = vzero<CPT>();
+          }
+          if ((fend >> (r + g)) & 1u) {  // F-block complete: its secondary targets
+            const int64_t fb = __shfl_sync(kFull, tj, r + g) / a;
+            flush_sec(fb);
+          }
+        }
+      }
+      kahan_fold<CPT>(acc, comp, part);
+    }
+  }
+  if (it.npieces > 1) {
+    // a piece of an F-block: partial secondary sums, combined in piece order
+    // by the last piece to finish
+    float *pbase = A.partial + ((int64_t)tile * P.n_partials + it.partial) * W;
+    for (int k = 0; k < nb2; ++k) strow<CPT>(pbase + (int64_t)k * W, lane, ldrow<CPT>(sec + (int64_t)k * W, lane));
+    __threadfence();
+    __syncwarp();
+    unsigned old = 0;
+    if (lane == 0) old = atomicAdd(&A.counters[(int64_t)tile * P.n_groups + it.group], 1u);
+    old = __shfl_sync(kFull, old, 0);
+    if (old == (unsigned)(it.npieces - 1)) {
+      __threadfence();
+      const int64_t fb = it.t0 / a;
+      const int first = it.partial - it.piece * nb2;
+      const int kind2 = P.tasks[it.task].sec_kind;
+      for (int k = 0; k < nb2; ++k) {
+        Vec<CPT> tot = vzero<CPT>();
+        for (int q = 0; q < it.npieces; ++q) {
+          const Vec<CPT> x =
+              ldrow<CPT, LD_CG>(A.partial + ((int64_t)tile * P.n_partials + first + q * nb2 + k) * W, lane);
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) tot.x[c] += x.x[c];
+        }
+        write(kind2, sec_row(fb, k), tot);
+      }
+      if (lane == 0) A.counters[(int64_t)tile * P.n_groups + it.group] = 0u;
+    }
+  }
+}
+
+// A distribute unit: a fused pair's item or a single task's item.
+template <int CPT, LoadMode RHO>
+__device__ __forceinline__ void distribute_unit(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
+                                                int lane, float *sec) {
+  if (it.fused) distribute_fused_item<CPT, RHO>(P, A, it, tile, lane, sec);
+  else distribute_item<CPT, RHO>(P, A, it, tile, lane);
+}
+
+// FUSED: the instantiation for plans whose work lists hold fused items;
+// plans without them run the plain item only, at the plain item's
+// register budget and occupancy.
+template <int CPT, bool FUSED>
+__global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocksPerSM : kDistributeBlocksPerSM)
+    k_distribute(DevPlan P, DevArena A, int64_t item_begin, int64_t n_items) {
+  extern __shared__ __align__(16) float dsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (iw >= n_items) return;
-  distribute_item<CPT, LD_NC>(P, A, P.ditems[item_begin + iw], blockIdx.y, lane);
+  if constexpr (FUSED)
+    distribute_unit<CPT, LD_NC>(P, A, P.ditems[item_begin + iw], blockIdx.y, lane,
+                                dsm + (size_t)warp * P.sec_rows * (32 * CPT));
+  else
+    distribute_item<CPT, LD_NC>(P, A, P.ditems[item_begin + iw], blockIdx.y, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -727,9 +931,12 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect_flow(
   }
 }
 
-template <int CPT>
-__global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute_flow(DevPlan P, DevArena A) {
+template <int CPT, bool FUSED>
+__global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocksPerSM : kDistributeBlocksPerSM)
+    k_distribute_flow(DevPlan P, DevArena A) {
+  extern __shared__ __align__(16) float dsm[];
   const int lane = threadIdx.x & 31;
+  float *sec = dsm + (size_t)(threadIdx.x >> 5) * P.sec_rows * (32 * CPT);
   int64_t item;
   int tile;
   while (next_unit(A.queue + 16, P.d_flow_pref, P.d_flow_begin, P.n_flow_layers, A.tiles, lane, item, tile)) {
@@ -737,10 +944,49 @@ __global__ void __launch_bounds__(kThreads, kDistributeBlocksPerSM) k_distribute
     const DTask &T = P.tasks[it.task];
     uint32_t *ready = A.ready + ((int64_t)tile * 2 + 1) * P.n_cliques;
     const uint32_t need = P.d_need[T.clique];
-    if (need == 0u || wait_ready(ready + T.clique, need, A.errflag, P.wait_limit_ns, lane))
-      distribute_item<CPT, LD_PLAIN>(P, A, it, tile, lane);
+    if (need == 0u || wait_ready(ready + T.clique, need, A.errflag, P.wait_limit_ns, lane)) {
+      if constexpr (FUSED) distribute_unit<CPT, LD_PLAIN>(P, A, it, tile, lane, sec);
+      else distribute_item<CPT, LD_PLAIN>(P, A, it, tile, lane);
+    }
+    // a fused item also completes its share of the secondary child's ratio
+    if (FUSED && it.fused && T.sec_kind == TASK_CHILD) {
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) atomicAdd(ready + T.sec_dst, 1u);
+    }
     signal_done(T.kind == TASK_CHILD ? ready + T.dst : nullptr, lane);
   }
+}
+
+// ---------------------------------------------------------------------------
+// explicit unit lists (iteration-level batching of the serving loop): one
+// launch per pass covers a list of (work item, tile) units, each tile of the
+// list at its own tree layer; a warp takes one unit.
+// ---------------------------------------------------------------------------
+template <int CPT, bool SLICED>
+__global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect_units(DevPlan P, DevArena A, const int2 *units,
+                                                                                 int n_units, int max_maps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (u >= n_units) return;
+  const int2 un = units[u];
+  collect_item<CPT, LD_NC, SLICED>(P, A, P.citems[un.x], un.y,
+                                   smem_raw + (size_t)warp * collect_warp_smem(CPT, max_maps), max_maps, lane);
+}
+
+template <int CPT, bool FUSED>
+__global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocksPerSM : kDistributeBlocksPerSM)
+    k_distribute_units(DevPlan P, DevArena A, const int2 *units, int n_units) {
+  extern __shared__ __align__(16) float dsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (u >= n_units) return;
+  const int2 un = units[u];
+  if constexpr (FUSED)
+    distribute_unit<CPT, LD_NC>(P, A, P.ditems[un.x], un.y, lane, dsm + (size_t)warp * P.sec_rows * (32 * CPT));
+  else
+    distribute_item<CPT, LD_NC>(P, A, P.ditems[un.x], un.y, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -995,6 +1241,24 @@ static int collect_warps(int cpt, int max_maps) {
   return (int)std::min<size_t>(kWarps, std::max<size_t>(1, kCollectSmemLimit / std::max<size_t>(per_warp, 1)));
 }
 
+size_t distribute_smem_bytes(int cpt, int sec_rows) {
+  return (size_t)kWarps * (size_t)sec_rows * 32 * (size_t)cpt * sizeof(float);
+}
+
+// Calls f(CPT, FUSED) with both as compile-time constants.
+template <class F>
+static auto with_distribute(int cpt, bool fused, F &&f) {
+  using std::integral_constant;
+  using yes = std::true_type;
+  using no = std::false_type;
+  if (cpt == 8) return fused ? f(integral_constant<int, 8>{}, yes{}) : f(integral_constant<int, 8>{}, no{});
+  if (cpt == 4) return fused ? f(integral_constant<int, 4>{}, yes{}) : f(integral_constant<int, 4>{}, no{});
+  if (cpt == 2) return fused ? f(integral_constant<int, 2>{}, yes{}) : f(integral_constant<int, 2>{}, no{});
+  return fused ? f(integral_constant<int, 1>{}, yes{}) : f(integral_constant<int, 1>{}, no{});
+}
+
+static bool has_fused(const DevPlan &P) { return P.fused_items > 0; }
+
 // Calls f(CPT, SLICED) with both as compile-time constants: the collect
 // kernels are instantiated per cases-per-thread and per plan kind.
 template <class F>
@@ -1015,11 +1279,37 @@ cudaError_t configure_collect_smem(int cpt, bool sliced, size_t bytes) {
   return with_collect(cpt, sliced, [&](auto c, auto sl) {
     constexpr int CPT = decltype(c)::value;
     constexpr bool SL = decltype(sl)::value;
-    const cudaError_t e =
+    cudaError_t e =
         cudaFuncSetAttribute((const void *)k_collect<CPT, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void *)k_collect_units<CPT, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute((const void *)k_collect_flow<CPT, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)bytes);
+  });
+}
+
+void launch_collect_units(int cpt, const DevPlan &P, const DevArena &A, const int2 *units, int n_units, int max_maps,
+                          cudaStream_t s) {
+  if (n_units <= 0) return;
+  with_collect(cpt, is_sliced(P), [&](auto c, auto sl) {
+    constexpr int CPT = decltype(c)::value;
+    const int nw = collect_warps(CPT, max_maps);
+    const size_t smem = (size_t)nw * collect_warp_smem(CPT, max_maps);
+    k_collect_units<CPT, decltype(sl)::value><<<(unsigned)((n_units + nw - 1) / nw), 32 * nw, smem, s>>>(
+        P, A, units, n_units, max_maps);
+  });
+}
+
+void launch_distribute_units(int cpt, const DevPlan &P, const DevArena &A, const int2 *units, int n_units,
+                             cudaStream_t s) {
+  if (n_units <= 0) return;
+  const unsigned grid = (unsigned)((n_units + kWarps - 1) / kWarps);
+  const bool fu = has_fused(P);
+  const size_t sm = fu ? distribute_smem_bytes(cpt, P.sec_rows) : 0;
+  with_distribute(cpt, fu, [&](auto c, auto f) {
+    k_distribute_units<decltype(c)::value, decltype(f)::value><<<grid, kThreads, sm, s>>>(P, A, units, n_units);
   });
 }
 
@@ -1035,13 +1325,32 @@ void launch_collect(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int
   });
 }
 
+
+
+cudaError_t configure_distribute_smem(int cpt, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return with_distribute(cpt, true, [&](auto c, auto fu) {
+    constexpr int CPT = decltype(c)::value;
+    constexpr bool FU = decltype(fu)::value;
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_distribute<CPT, FU>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void *)k_distribute_units<CPT, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)k_distribute_flow<CPT, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+  });
+}
+
 void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   dim3 grid((unsigned)((n + kWarps - 1) / kWarps), (unsigned)A.tiles);
-  if (cpt == 8) k_distribute<8><<<grid, kThreads, 0, s>>>(P, A, b, n);
-  else if (cpt == 4) k_distribute<4><<<grid, kThreads, 0, s>>>(P, A, b, n);
-  else if (cpt == 2) k_distribute<2><<<grid, kThreads, 0, s>>>(P, A, b, n);
-  else k_distribute<1><<<grid, kThreads, 0, s>>>(P, A, b, n);
+  const bool fu = has_fused(P);
+  const size_t sm = fu ? distribute_smem_bytes(cpt, P.sec_rows) : 0;
+  with_distribute(cpt, fu, [&](auto c, auto f) {
+    k_distribute<decltype(c)::value, decltype(f)::value><<<grid, kThreads, sm, s>>>(P, A, b, n);
+  });
 }
 
 void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s) {
@@ -1054,10 +1363,11 @@ void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int block
 }
 
 void launch_distribute_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, cudaStream_t s) {
-  if (cpt == 8) k_distribute_flow<8><<<blocks, kThreads, 0, s>>>(P, A);
-  else if (cpt == 4) k_distribute_flow<4><<<blocks, kThreads, 0, s>>>(P, A);
-  else if (cpt == 2) k_distribute_flow<2><<<blocks, kThreads, 0, s>>>(P, A);
-  else k_distribute_flow<1><<<blocks, kThreads, 0, s>>>(P, A);
+  const bool fu = has_fused(P);
+  const size_t sm = fu ? distribute_smem_bytes(cpt, P.sec_rows) : 0;
+  with_distribute(cpt, fu, [&](auto c, auto f) {
+    k_distribute_flow<decltype(c)::value, decltype(f)::value><<<blocks, kThreads, sm, s>>>(P, A);
+  });
 }
 
 // Resident blocks per SM of the dataflow kernels (their grids fill the GPU once).
@@ -1071,7 +1381,7 @@ static int occupancy_of(K kernel, int threads, size_t smem) {
   return n > 0 ? n : 1;
 }
 
-int flow_blocks_per_sm(int cpt, bool collect, bool sliced, int max_maps) {
+int flow_blocks_per_sm(int cpt, bool collect, bool sliced, int max_maps, int sec_rows) {
   if (collect) {
     const int nw = collect_warps(cpt, max_maps);
     const size_t smem = (size_t)nw * collect_warp_smem(cpt, max_maps);
@@ -1079,10 +1389,11 @@ int flow_blocks_per_sm(int cpt, bool collect, bool sliced, int max_maps) {
       return occupancy_of(k_collect_flow<decltype(c)::value, decltype(sl)::value>, 32 * nw, smem);
     });
   }
-  if (cpt == 8) return occupancy_of(k_distribute_flow<8>, kThreads, 0);
-  if (cpt == 4) return occupancy_of(k_distribute_flow<4>, kThreads, 0);
-  if (cpt == 2) return occupancy_of(k_distribute_flow<2>, kThreads, 0);
-  return occupancy_of(k_distribute_flow<1>, kThreads, 0);
+  const bool fu = sec_rows > 0;
+  const size_t sm = fu ? distribute_smem_bytes(cpt, sec_rows) : 0;
+  return with_distribute(cpt, fu, [&](auto c, auto f) {
+    return occupancy_of(k_distribute_flow<decltype(c)::value, decltype(f)::value>, kThreads, sm);
+  });
 }
 
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,

@@ -38,7 +38,8 @@ class CompileOpts(ctypes.Structure):
                 ("n_observed_set", ctypes.c_int32), ("observed_set", ctypes.c_void_p),
                 ("rescale", ctypes.c_int32), ("n_query_set", ctypes.c_int32), ("query_set", ctypes.c_void_p),
                 ("collect_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
-                ("distribute_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS)]
+                ("distribute_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
+                ("fuse_distribute", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -69,8 +70,8 @@ class PlanInfo(ctypes.Structure):
 EXPORTS = ["jt_default_opts", "jt_compile", "jt_autotune", "jt_infer", "jt_infer_device", "jt_infer_plain", "jt_infer_cpu",
            "jt_profile", "jt_debug_stall",
            "jt_plan_info", "jt_plan_clique", "jt_plan_free", "jt_status_string", "jt_last_error",
-           "jt_server_create", "jt_server_add_plan", "jt_submit", "jt_poll", "jt_server_drain",
-           "jt_server_stats", "jt_server_destroy"]
+           "jt_server_create", "jt_server_add_plan", "jt_server_add_plan_rolling", "jt_submit", "jt_poll", "jt_server_drain",
+           "jt_server_stats", "jt_server_plan_stats", "jt_server_reset_latency", "jt_server_destroy"]
 
 
 def _load():
@@ -96,10 +97,13 @@ def _load():
         "jt_last_error": ([], ctypes.c_char_p),
         "jt_server_create": ([I64, I32, I32, ctypes.POINTER(P)], ctypes.c_int),
         "jt_server_add_plan": ([P, P, ctypes.POINTER(I32)], ctypes.c_int),
+        "jt_server_add_plan_rolling": ([P, P, I32, ctypes.POINTER(I32)], ctypes.c_int),
         "jt_submit": ([P, I32, P, P, I32, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "jt_poll": ([P, ctypes.c_uint64, P, P, P], ctypes.c_int),
         "jt_server_drain": ([P], ctypes.c_int),
         "jt_server_stats": ([P, P], ctypes.c_int),
+        "jt_server_plan_stats": ([P, I32, P], ctypes.c_int),
+        "jt_server_reset_latency": ([P], ctypes.c_int),
         "jt_server_destroy": ([P], None),
     }
     for name in EXPORTS:
@@ -175,7 +179,7 @@ def autotune(net, n_cases: int, **opts):
                            int(n_cases), ctypes.byref(best), ctypes.byref(ns)))
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
                                            "items_per_tile_distribute", "use_graphs", "arena_bytes",
-                                           "max_clique_entries", "schedule", "rescale")}
+                                           "max_clique_entries", "schedule", "rescale", "fuse_distribute")}
     for k in ("collect_rows_by_bucket", "distribute_rows_by_bucket"):
         out[k] = [int(x) for x in getattr(best, k)]
     for k in ("observed_set", "query_set"):
@@ -303,9 +307,14 @@ class Server:
         self._h = h
         self._plans = []
 
-    def add_plan(self, plan: Plan) -> int:
+    def add_plan(self, plan: Plan, rolling_tiles: int = 0) -> int:
+        """Register a plan: batch slots (jt_server_add_plan), or iteration-level
+        batching over `rolling_tiles` resident tiles (jt_server_add_plan_rolling)."""
         pid = ctypes.c_int32()
-        _check(lib.jt_server_add_plan(self._h, plan.handle, ctypes.byref(pid)))
+        if rolling_tiles > 0:
+            _check(lib.jt_server_add_plan_rolling(self._h, plan.handle, int(rolling_tiles), ctypes.byref(pid)))
+        else:
+            _check(lib.jt_server_add_plan(self._h, plan.handle, ctypes.byref(pid)))
         self._plans.append(plan)
         return int(pid.value)
 
@@ -334,10 +343,19 @@ class Server:
         _check(lib.jt_server_drain(self._h))
 
     def stats(self) -> dict:
-        out = np.zeros(7, dtype=np.int64)
+        out = np.zeros(9, dtype=np.int64)
         _check(lib.jt_server_stats(self._h, _ptr(out)))
-        keys = ["completed", "batches", "largest_batch", "peak_arena_bytes", "p50_ns", "p99_ns", "outstanding"]
+        keys = ["completed", "batches", "largest_batch", "peak_arena_bytes", "p50_ns", "p99_ns", "outstanding",
+                "slot_creations", "slot_evictions"]
         return dict(zip(keys, (int(x) for x in out)))
+
+    def reset_latency(self):
+        _check(lib.jt_server_reset_latency(self._h))
+
+    def plan_stats(self, plan_id: int) -> dict:
+        out = np.zeros(4, dtype=np.int64)
+        _check(lib.jt_server_plan_stats(self._h, int(plan_id), _ptr(out)))
+        return dict(zip(["completed", "batches", "p50_ns", "p99_ns"], (int(x) for x in out)))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -155,6 +155,33 @@ def test_admission_by_arena_bytes(plans):
     assert len(res) == 100
     st = srv.stats()
     assert st["peak_arena_bytes"] <= budget
+    # slots are bound once and reused; when the pool cannot hold both plans'
+    # slots the plans take turns, evicting each other's idle slot
+    assert st["slot_creations"] - st["slot_evictions"] in (1, 2)
+    assert st["slot_creations"] <= st["batches"]
+    for pid in (a, b):
+        ps = srv.plan_stats(pid)
+        assert ps["completed"] == 50 and ps["batches"] >= 1 and ps["p99_ns"] >= ps["p50_ns"] > 0
+    srv.close()
+
+
+def test_slots_are_reused_batch_after_batch(plans):
+    """A plan's batch slots are regions of the server's pool bound once and
+    reused: many waves of requests create at most max_inflight slots."""
+    nm, net, plan = plans[0]
+    srv = J.Server(arena_bytes=8 << 30, max_batch=16, max_inflight=3)
+    pid = srv.add_plan(plan)
+    ev = configs.evidence(nm, net, n_cases=64, seed=9)
+    for wave in range(6):
+        tickets = [srv.submit(pid, e) for e in ev]
+        res = _wait(srv, tickets, {t: plan.sum_card for t in tickets})
+        assert all(r[2] == 0 for r in res.values())
+    st = srv.stats()
+    assert st["completed"] == 6 * 64 and st["batches"] >= 6 * 4
+    assert 1 <= st["slot_creations"] <= 3 and st["slot_evictions"] == 0
+    with pytest.raises(J.JTError) as e:
+        srv.plan_stats(pid + 1)
+    assert e.value.status == J.JT_ENOTFOUND
     srv.close()
 
 
@@ -182,4 +209,77 @@ def test_expired_device_wait_in_a_served_batch():
         post = np.stack([res[t][1] for t in tg])
         st = np.array([res[t][2] for t in tg], dtype=np.int32)
         assert_parity32(lp, post, st, olp, opost, ost, where="served beside a stalled plan")
+    srv.close()
+
+
+def test_rolling_alone_vs_mix_and_slots_bitwise(plans):
+    """Iteration-level batching: requests that arrive while other tiles are
+    mid-pass join at the next tick.  Each result equals the same request
+    served alone, and the batch-slot path's result, bit for bit, and the
+    FP64 oracle within the FP32 tolerance."""
+    rng = np.random.default_rng(1)
+    reqs = []
+    for pi, (nm, net, plan) in enumerate(plans):
+        ev = configs.evidence(nm, net, n_cases=60, seed=900 + pi)
+        reqs += [(pi, e) for e in ev]
+    srv = J.Server(arena_bytes=8 << 30, max_batch=32, max_inflight=4)
+    rolled = [srv.add_plan(p, rolling_tiles=4) for _, _, p in plans]
+    slotted = [srv.add_plan(p) for _, _, p in plans]
+    out_len = lambda pi: plans[pi][2].sum_card  # noqa: E731
+    alone = {}
+    for i, (pi, e) in enumerate(reqs[::7]):
+        t = srv.submit(rolled[pi], e)
+        srv.drain()
+        alone[i * 7] = srv.poll(t, out_len(pi))
+    # the mix: submitted in waves with pauses, so that new requests arrive
+    # while earlier tiles are between layers
+    tickets, lens, which = [], {}, {}
+    order = rng.permutation(len(reqs))
+    for w, chunk in enumerate(np.array_split(order, 6)):
+        for i in chunk:
+            pi, e = reqs[i]
+            t = srv.submit(rolled[pi], e)
+            tickets.append(t)
+            lens[t] = out_len(pi)
+            which[t] = i
+        time.sleep(0.002 * w)
+    res = _wait(srv, tickets, lens)
+    # the batch-slot path on the same requests
+    st_tickets, st_which = [], {}
+    for i in range(len(reqs)):
+        pi, e = reqs[i]
+        t = srv.submit(slotted[pi], e)
+        st_tickets.append(t)
+        lens[t] = out_len(pi)
+        st_which[t] = i
+    slot_res = _wait(srv, st_tickets, lens)
+    by_req = {which[t]: r for t, r in res.items()}
+    for t, r in slot_res.items():
+        a = by_req[st_which[t]]
+        assert a[0] == r[0] and a[2] == r[2] and np.array_equal(a[1], r[1]), "rolling vs batch slots"
+    for i, a in alone.items():
+        b = by_req[i]
+        assert a[0] == b[0] and a[2] == b[2] and np.array_equal(a[1], b[1]), "alone vs mix"
+    for pi, (nm, net, plan) in enumerate(plans):
+        idx = [i for i in range(len(reqs)) if reqs[i][0] == pi]
+        ev = np.stack([reqs[i][1] for i in idx])
+        olp, opost, ost = oracle.Oracle(net).infer(ev, threads=8)
+        lp = np.array([by_req[i][0] for i in idx])
+        post = np.stack([by_req[i][1] for i in idx])
+        cs = np.array([by_req[i][2] for i in idx], dtype=np.int32)
+        assert_parity32(lp, post, cs, olp, opost, ost, where=f"rolling {nm}")
+    st = srv.stats()
+    assert st["completed"] == len(alone) + 2 * len(reqs)
+    for pid in rolled:
+        ps = srv.plan_stats(pid)
+        assert ps["p99_ns"] >= ps["p50_ns"] > 0
+    srv.close()
+
+
+def test_rolling_refuses_tiles_beyond_the_pool(plans):
+    nm, net, plan = plans[1]
+    srv = J.Server(arena_bytes=1 << 26, max_batch=8, max_inflight=2)
+    with pytest.raises(J.JTError) as e:
+        srv.add_plan(plan, rolling_tiles=1 << 16)
+    assert e.value.status == J.JT_ENOMEM
     srv.close()

@@ -66,3 +66,19 @@ def test_specialised_plan_maps(checker, name, obs, query, tmp_path):
 @pytest.mark.parametrize("seed", range(30))
 def test_tiny_network_maps(checker, seed, tmp_path):
     _run(checker, tiny_random_network(seed), tmp_path)
+
+
+@pytest.mark.parametrize("name,args", [("bn60", ["cpt=1", "rows=4096"]), ("bn60", ["cpt=1", "rows=128"]),
+                                       ("bn110", ["cpt=2", "rows=256"]), ("bn420", ["cpt=4"]),
+                                       ("bn420", ["cpt=1", "rows=128"]), ("bn60", ["fuse=0"]),
+                                       ("bn420", ["rows=64"])])
+def test_fused_pair_maps(checker, name, args, tmp_path):
+    """Fused distribute pairs (two marginals of one clique table from one
+    read): every index of the reordered primary, the secondary's per-F-block
+    targets, and the pieces of F-blocks larger than an item."""
+    _run(checker, configs.network(name), tmp_path, *args)
+
+
+@pytest.mark.parametrize("seed", range(30, 60))
+def test_tiny_network_fused_maps(checker, seed, tmp_path):
+    _run(checker, tiny_random_network(seed), tmp_path, "cpt=1", "rows=128" if seed % 2 else "rows=4096")

@@ -50,3 +50,58 @@ def test_two_rank_sharding_and_timing():
 def test_single_rank_is_identity():
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert bench.aggregate_rate(100, 1, 10.0) == 100 / 0.01
+
+
+def _rank_path(rank, world, port, out):
+    """The bench's rank path with a stand-in step: own seeds, the timed
+    region (barrier, steps, barrier, max over ranks), the job's rate and,
+    on rank 0, the line."""
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    net = configs.network("bn20")
+    n_cases, steps = 32, 3
+    ev = configs.evidence("bn20", net, n_cases=n_cases, seed=bench.rank_evidence_seed("bn20", rank))
+
+    def step():                      # a stand-in for one pass: rank 1 is slower
+        time.sleep(0.004 * (1 + rank))
+        return int(ev.sum())
+
+    ms = bench.timed_region(step, steps, dist, "cpu", bench.WallTimer())
+    value = bench.aggregate_rate(n_cases, world, ms / steps)
+    line = bench.base_line(value, world, steps, 3, ms / steps) if rank == 0 else None
+    out[rank] = (ms, value, line, ev.tobytes())
+    dist.destroy_process_group()
+
+
+def test_two_rank_bench_path():
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_rank_path, args=(world, _free_port(), out), nprocs=world, join=True)
+    ms0, v0, line, ev0 = out[0]
+    ms1, v1, none, ev1 = out[1]
+    assert ms0 == ms1 >= 3 * 8.0            # the slowest rank's region, on every rank
+    assert v0 == v1 == 32 * 2 / (ms0 / 3 / 1e3)
+    assert none is None and ev0 != ev1      # one line (rank 0); independent batches
+    assert line["n_gpus"] == 2 and line["scaling"] == "weak" and line["value"] == v0
+    assert line["metric"] == bench.METRIC and line["ms_per_step"] == ms0 / 3
+
+
+def test_gpus_flag_spawns_ranks():
+    """`bench.py --gpus 2` outside torchrun relaunches itself as two ranks;
+    the reference arm (the oracle on the host) needs no GPU, so the whole
+    launch runs here: one line, from rank 0, with n_gpus = 2."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--impl", "reference",
+                        "--workload", "bn20", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["impl"] == "reference" and d["metric"] == bench.METRIC
