@@ -291,18 +291,24 @@ def _oracle_rate(net, ev, threads, budget_s):
 SERVING_PLANS = ["bn60", "bn110", "bn420", "bn1000"]
 
 
-ROLLING_TILES = {"bn60": 16, "bn1000": 16, "bn110": 6, "bn420": 4}
+# resident tiles per plan served with iteration-level batching (as many as
+# the pool holds, up to these); a plan absent here is served with batch
+# slots.  The rolling tiles stay resident, so that mode gets the larger pool
+# (batch slots measured lower latency with 48 GB than with 96 GB: more slots
+# in flight put more of the large plans' work in front of the small ones).
+ROLLING_TILES = {"bn60": 16, "bn1000": 16, "bn110": 8, "bn420": 6}
+SERVING_POOL_GB = 96.0
 
 
 def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, max_batch: int = 64,
-                arena_gb: float = 48.0, schedule=None, min_requests: int = 20000, rolling: bool = False):
+                arena_gb: float = SERVING_POOL_GB, schedule=None, min_requests: int = 20000, rolling: bool = False):
     """The serving mix: resident plans of the four networks, one-case requests
     on a uniformly chosen plan with 5-30 % observed, Poisson arrivals at
     fractions of the measured saturated rate.  Returns p50/p99 latency
     (submit -> result on the host) and cases/s per offered rate, overall and
-    per plan.  rolling: every plan is served with iteration-level batching
-    (resident tiles that advance one tree layer per tick; requests join at
-    the next tick) instead of batch slots."""
+    per plan.  rolling: the plans of ROLLING_TILES are served with
+    iteration-level batching (resident tiles that advance one tree layer per
+    tick; requests join at the next tick), the others with batch slots."""
     import paper_2212_04241_gb300.jt as J
     from synth import configs
     from synth.bn import sample_cases
@@ -342,16 +348,21 @@ def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, 
         if not rolling:
             return srv, [srv.add_plan(pl) for pl in plans]
         pids = [None] * len(plans)
-        for i in sorted(range(len(plans)), key=lambda j: -ROLLING_TILES[SERVING_PLANS[j]]):
-            for t in range(ROLLING_TILES[SERVING_PLANS[i]], 0, -1):   # as many tiles as the pool holds
+        for i, nm in enumerate(SERVING_PLANS):   # the small plans first
+            if nm not in ROLLING_TILES:
+                continue
+            for t in range(ROLLING_TILES[nm], 0, -1):   # as many tiles as the pool holds
                 try:
                     pids[i] = srv.add_plan(plans[i], rolling_tiles=t)
-                    tiles_used[SERVING_PLANS[i]] = t
+                    tiles_used[nm] = t
                     break
                 except J.JTError:
                     continue
             if pids[i] is None:
-                raise RuntimeError(f"rolling plan {SERVING_PLANS[i]} does not fit the pool")
+                raise RuntimeError(f"rolling plan {nm} does not fit the pool")
+        for i, nm in enumerate(SERVING_PLANS):
+            if pids[i] is None:
+                pids[i] = srv.add_plan(plans[i])
         return srv, pids
 
     tiles_used = {}
@@ -361,14 +372,15 @@ def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, 
     n_sat = 20000
     sat = n_sat / drive(srv, pids, n_sat, None)
     srv.close()
-    out = {"plans": SERVING_PLANS, "arena_gb": arena_gb,
-           "mode": "rolling tiles (iteration-level batching)" if rolling else "batch slots",
+    out = {"plans": SERVING_PLANS, "arena_gb": arena_gb, "max_batch": max_batch,
+           "mode": ("rolling tiles (iteration-level batching) for " + ", ".join(sorted(ROLLING_TILES)) +
+                    (", batch slots for the others" if set(ROLLING_TILES) != set(SERVING_PLANS) else ""))
+           if rolling else "batch slots",
            "saturated_cases_per_s": sat, "rates": []}
     if rolling:
         out["tiles"] = dict(tiles_used)
         out["tile_cases"] = {nm: int(pl.info()["tile_cases"]) for nm, pl in zip(SERVING_PLANS, plans)}
-    else:
-        out["max_batch"] = max_batch
+    if set(ROLLING_TILES) != set(SERVING_PLANS) or not rolling:
         out["schedule"] = "layers" if sched == J.JT_SCHEDULE_LAYERS else "dataflow"
     for f in rates:
         rate = f * sat
@@ -497,7 +509,7 @@ def main():
 
     import torch
     if args.serving_only:
-        print(json.dumps({"serving": {"batch_slots": run_serving(), "rolling": run_serving(rolling=True)}}),
+        print(json.dumps({"serving": {"batch_slots": run_serving(arena_gb=48.0), "rolling": run_serving(rolling=True)}}),
               flush=True)
         return 0
     torch.cuda.set_device(local_rank)
@@ -653,7 +665,7 @@ def main():
 
     serving = None
     if rank == 0 and not args.no_serving and world == 1:
-        serving = {"batch_slots": run_serving(), "rolling": run_serving(rolling=True)}
+        serving = {"batch_slots": run_serving(arena_gb=48.0), "rolling": run_serving(rolling=True)}
 
     if dist:
         dist.destroy_process_group()

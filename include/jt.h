@@ -473,7 +473,9 @@ JT_API jt_status jt_server_add_plan(jt_server *srv, jt_plan *plan, int32_t *plan
  * kernels -- and one tick is two launches over every active tile, each at
  * its own layer.  A request arriving while other tiles are mid-pass starts
  * at the next tick, in a free tile, instead of waiting for a whole pass.
- * At most two ticks of a plan are in flight.  Results are the same bit for
+ * At most two ticks of a plan are in flight; they run on a stream of the
+ * highest priority, so their blocks are dispatched ahead of the batch
+ * slots' passes.  Results are the same bit for
  * bit as the batch-slot path's (same kernels per tile, fixed per-case
  * reduction order).  Allocates the plan's staging buffers and stream.
  * JT_ENOMEM when the tiles do not fit the free part of the pool.  The plan

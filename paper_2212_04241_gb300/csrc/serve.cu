@@ -184,13 +184,21 @@ size_t slot_arena_bytes(const jt_plan *pl, int max_batch) {
 }
 
 // Bind a new slot of plan `pid` to a pool region (no allocation: host
-// bookkeeping only); evicts idle slots of other plans, least recently used
-// first, when the pool has no region large enough.
+// bookkeeping only).  When the pool has no region large enough, idle slots
+// of other plans are evicted, least recently used first -- by a plan
+// without any slot, or by one with a full batch of requests waiting behind
+// its busy slots; a plan with a slot and a short queue waits for it
+// instead, so resident slots are not traded back and forth under light
+// load.
 Slot *slot_create(jt_server *S, int pid) {
   jt_plan *pl = S->plans[pid].plan;
   const size_t need = slot_arena_bytes(pl, S->max_batch);
   size_t off = 0;
+  bool has_slot = false;
+  for (auto &sp : S->slots) has_slot = has_slot || sp->plan_id == pid;
+  const bool backlog = (int64_t)S->plans[pid].pending.size() >= S->max_batch;
   while (!pool_alloc(S, need, &off)) {
+    if (has_slot && !backlog) return nullptr;
     Slot *victim = nullptr;
     size_t vi = 0;
     for (size_t j = 0; j < S->slots.size(); ++j) {
@@ -666,7 +674,13 @@ static jt_status jt_server_add_plan_rolling_impl(jt_server *S, jt_plan *pl, int3
     set_error(msg);
     return st;
   };
-  if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
+  // the ticks of a rolling plan are short launches: on a stream of the
+  // highest priority their blocks are dispatched before those of the batch
+  // slots' long passes, so a tick does not queue behind a whole layer of a
+  // large plan
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (cudaStreamCreateWithPriority(&r->stream, cudaStreamNonBlocking, greatest) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev[1], cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
