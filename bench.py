@@ -57,10 +57,19 @@ METRIC = "evidence cases/sec at \u22641e-5 posterior error, batched vs plain; p5
 
 # DRAM traffic of the dominant kernel per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture), valid only for the plan shape
-# and kernel source it was taken with: keyed by (workload, cases, a key of
-# the plan's distribute work shape, sha256 prefix of csrc/kernels.cu);
-# anything else reports null.
-MEASURED_TRAFFIC = {}
+# and kernel source it was taken with: keyed by (workload, cases, the plan's
+# distribute work shape, sha256 prefix of csrc/kernels.cu); anything else
+# reports null.
+MEASURED_TRAFFIC = {
+    ("bn420", 896, (768, (0,) * 32, 1), "c144a3405c3ce8c9"): 256720000000 + 25940000000,
+}
+
+
+def _distribute_shape(tuned):
+    """The plan options that shape the distribute pass's work lists."""
+    items = int(tuned.get("items_per_tile_distribute") or tuned.get("items_per_tile") or 192)
+    table = tuple(int(x) for x in (tuned.get("distribute_rows_by_bucket") or (0,) * 32))
+    return (items, table, int(tuned.get("fuse_distribute", 1)))
 
 
 def _kept_columns(net, roots):
@@ -606,7 +615,7 @@ def main():
     # the plan's distribute work-item target (0 in the options = items_per_tile, whose 0 = 192)
     items_d = int(tuned.get("items_per_tile_distribute") or tuned.get("items_per_tile") or 192)
     ksha = _kernel_source_hash()
-    traffic = (MEASURED_TRAFFIC.get((name, n_cases, items_d, ksha))
+    traffic = (MEASURED_TRAFFIC.get((name, n_cases, _distribute_shape(tuned), ksha))
                if dataflow and dom == "distribute" and not observed_set else None)
     roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
@@ -684,6 +693,8 @@ def main():
                                  if tuned and not args.plan and not args.no_autotune else None),
                    "work_shape_by_bucket": _bucket_table(info),
                    "plan_options": tuned if args.plan else None,
+                   # the plan's options as used (replayable with --plan)
+                   "tuned_options": {k: v for k, v in tuned.items() if k not in ("observed_set", "query_set")},
                    "schedule": "dataflow" if dataflow else "layers",
                    "sum_clique_entries": info["sum_clique_entries"],
                    "l2": "inputs larger than L2 (psi arena %.2f GB per step)" % (4.0 * info["sum_clique_entries"] * n_cases / 1e9),

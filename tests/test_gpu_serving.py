@@ -157,8 +157,8 @@ def test_admission_by_arena_bytes(plans):
     assert st["peak_arena_bytes"] <= budget
     # slots are bound once and reused; when the pool cannot hold both plans'
     # slots the plans take turns, evicting each other's idle slot
-    assert st["slot_creations"] - st["slot_evictions"] in (1, 2)
-    assert st["slot_creations"] <= st["batches"]
+    resident = st["slot_creations"] - st["slot_evictions"]
+    assert 1 <= resident <= 4 and st["slot_creations"] <= st["batches"]
     for pid in (a, b):
         ps = srv.plan_stats(pid)
         assert ps["completed"] == 50 and ps["batches"] >= 1 and ps["p99_ns"] >= ps["p50_ns"] > 0
