@@ -214,6 +214,20 @@ typedef struct {
                                  per block of common variables fit a warp's
                                  shared-memory sums; 0: every marginal reads
                                  the table on its own */
+  int32_t recompute_psi;      /* 1: the collect pass stores no clique tables;
+                                 the distribute pass recomputes every row it
+                                 reads from the base table, the child
+                                 messages and the evidence, in the collect
+                                 pass's arithmetic order (so the values are
+                                 the same bit for bit).  The per-batch
+                                 tables then hold no clique tables (a case
+                                 needs about 4*sum|S| + ... bytes instead of
+                                 4*sum|C| more), so an arena admits several
+                                 times more cases, and neither pass moves
+                                 the clique tables through DRAM.  Fused
+                                 distribute pairs are not used with it;
+                                 ignored for plans specialised to an
+                                 observed set.  0 (default): stored. */
 } jt_compile_opts;
 
 typedef struct {
@@ -397,7 +411,8 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
  *      the tile shape rows x cases -- over the powers of two 32 .. 4096,
  *      each pass keeping its own best value (coordinate descent; a change
  *      is kept when it is at least 1 % faster);
- *   3. the result with fuse_distribute turned the other way (recompiled),
+ *   3. the result with fuse_distribute turned the other way, and with
+ *      recompute_psi turned the other way (each recompiled), the fastest
  *      kept if it is at least 1 % faster.
  * Between the candidates of stages 1 and 2 only the work lists are
  * rebuilt, not the plan.

@@ -34,7 +34,9 @@ static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 ArenaLayout arena_layout(const Plan &P) {
   ArenaLayout L{};
   const size_t W = (size_t)P.tile;
-  L.psi = align_up(sizeof(float) * W * (size_t)P.sum_cl);
+  // recomputed clique tables: no psi region (its base pointer still anchors
+  // the message offsets of the kernels)
+  L.psi = P.recompute ? 0 : align_up(sizeof(float) * W * (size_t)P.sum_cl);
   L.sep = align_up(sizeof(float) * W * (size_t)P.sep_rows);
   L.post = align_up(sizeof(float) * W * (size_t)P.sum_card);
   L.partial = align_up(sizeof(float) * W * (size_t)std::max<int64_t>(1, P.n_partials));
@@ -306,8 +308,7 @@ static jt_status upload_work(jt_plan *pl) {
   // the distribute grid fills the GPU once at its kernel's occupancy
   int sms = 0;
   JT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
-  pl->flow_distribute_blocks =
-      sms * flow_blocks_per_sm(P.cpt_per_thread, false, false, 0, D.fused_items > 0 ? P.sec_rows : 0);
+  pl->flow_distribute_blocks = sms * distribute_flow_blocks_per_sm(P.cpt_per_thread, D);
   return JT_OK;
 }
 
@@ -370,6 +371,17 @@ static jt_status upload_plan(jt_plan *pl) {
   D.n_dropped = (int32_t)P.io_dropped.size();
   D.n_nan_cols = (int32_t)P.io_nan_cols.size();
   D.sec_rows = P.sec_rows;
+  D.recompute = P.recompute;
+  int max_maps = 0;
+  for (const Level &lv : P.levels) max_maps = std::max(max_maps, lv.c_max_maps);
+  D.max_maps = max_maps;
+  if (P.recompute && recompute_warp_smem_bytes(P.cpt_per_thread, max_maps) * kWarps > kCollectSmemLimit) {
+    set_error("recompute_psi: a clique has too many maps for the distribute blocks' shared memory");
+    return JT_ETOOBIG;
+  }
+  // before the work lists: their upload sizes the distribute grid by the
+  // kernel's occupancy at its shared memory
+  JT_CUDA_TRY(configure_distribute_smem(P.cpt_per_thread, P.sec_rows, max_maps));
   jt_status wst = upload_work(pl);
   if (wst != JT_OK) return wst;
   D.n_flow_layers = P.height + 1;
@@ -384,8 +396,6 @@ static jt_status upload_plan(jt_plan *pl) {
   D.post_rows = P.sum_card;
   D.n_partials = std::max<int64_t>(1, P.n_partials);
   D.n_groups = std::max<int64_t>(1, P.n_groups);
-  int max_maps = 0;
-  for (const Level &lv : P.levels) max_maps = std::max(max_maps, lv.c_max_maps);
   const size_t smem = collect_smem_bytes(P.cpt_per_thread, max_maps);
   if (collect_warp_smem_bytes(P.cpt_per_thread, max_maps) > kCollectSmemLimit) {
     set_error("a clique has too many child messages and evidence variables for one warp's shared memory");
@@ -400,8 +410,7 @@ static jt_status upload_plan(jt_plan *pl) {
   JT_CUDA_TRY(configure_posterior_smem());
   int sms = 0;
   JT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device));
-  pl->flow_collect_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, true, P.n_sliced > 0, max_maps);
-  JT_CUDA_TRY(configure_distribute_smem(P.cpt_per_thread, distribute_smem_bytes(P.cpt_per_thread, P.sec_rows)));
+  pl->flow_collect_blocks = sms * flow_blocks_per_sm(P.cpt_per_thread, P.n_sliced > 0, max_maps);
   return JT_OK;
 }
 
@@ -1124,19 +1133,27 @@ static jt_status jt_autotune_impl(int32_t n_vars, const int32_t *card, const int
   }
   // stage 3: the tuned shape with fused distribute pairs turned the other
   // way (fused items need the distribute kernel that runs at fewer blocks
-  // per SM; which one wins depends on the network)
+  // per SM), and with recomputed clique tables; which one wins depends on
+  // the network
   if (result == JT_OK && best_cw > 0) {
-    jt_compile_opts alt = best_o;
-    alt.fuse_distribute = best_o.fuse_distribute ? 0 : 1;
-    jt_plan *pl = nullptr;
-    jt_status st = jt_compile(n_vars, card, parent_ptr, parents, cpt, &alt, &pl);
-    double c_ms = -1, d_ms = -1;
-    if (st == JT_OK) st = time_plan(pl, c_ms, d_ms);
-    if (pl) jt_plan_free(pl);
-    if (st != JT_OK) result = st;
-    else if (c_ms + d_ms < 0.99 * best_total) {
-      best_o = alt;
-      best_total = c_ms + d_ms;
+    jt_compile_opts alts[2] = {best_o, best_o};
+    alts[0].fuse_distribute = best_o.fuse_distribute ? 0 : 1;
+    alts[1].recompute_psi = best_o.recompute_psi ? 0 : 1;
+    const jt_compile_opts base_best = best_o;
+    for (const jt_compile_opts &alt0 : alts) {
+      jt_compile_opts alt = alt0;
+      if (&alt0 == &alts[1]) alt.fuse_distribute = base_best.fuse_distribute;
+      jt_plan *pl = nullptr;
+      jt_status st = jt_compile(n_vars, card, parent_ptr, parents, cpt, &alt, &pl);
+      double c_ms = -1, d_ms = -1;
+      if (st == JT_OK) st = time_plan(pl, c_ms, d_ms);
+      if (pl) jt_plan_free(pl);
+      if (st == JT_ETOOBIG || st == JT_ENOMEM) continue;  // this variant does not fit: keep the others
+      if (st != JT_OK) { result = st; break; }
+      if (c_ms + d_ms < 0.99 * best_total) {
+        best_o = alt;
+        best_total = c_ms + d_ms;
+      }
     }
   }
   cudaFree(d_ev);

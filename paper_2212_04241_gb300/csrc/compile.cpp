@@ -929,6 +929,13 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
     return JT_EINVAL;
   }
   P.tile = 32 * P.cpt_per_thread;
+  if (opts.recompute_psi != 0 && opts.recompute_psi != 1) {
+    err = "recompute_psi must be 0 or 1";
+    return JT_EINVAL;
+  }
+  // recomputed clique tables: standard plans (a sliced plan's base-table
+  // gather stays in the collect pass)
+  P.recompute = (opts.recompute_psi && P.n_sliced == 0) ? 1 : 0;
   // distribute tasks: children first (ascending), then owned posteriors
   std::vector<std::vector<int>> tasks_of(m);
   std::vector<std::vector<int>> task_vars;  // target variables of each task
@@ -992,7 +999,7 @@ jt_status build_plan(int32_t n, const int32_t *card, const int32_t *pptr, const 
   // memory, kFusedRowBytes per warp at most, so its targets per F-block
   // are bounded by that over the tile's row bytes.
   P.sec_rows = 0;
-  if (opts.fuse_distribute) {
+  if (opts.fuse_distribute && !P.recompute) {
     const int64_t bmax = kFusedRowBytes / (4 * (int64_t)P.tile);
     for (int c = 0; c < m; ++c) {
       const HostClique &C = P.cl[c];

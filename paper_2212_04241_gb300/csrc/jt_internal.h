@@ -245,6 +245,7 @@ struct Plan {
 
   jt_compile_opts opts{};
   int cpt_per_thread = 4;
+  int recompute = 0;              // 1: no stored clique tables; distribute recomputes them
   int sec_rows = 0;               // largest sec_b of the fused tasks (shared-memory rows per warp)
   int tile = 128;
   int rows_per_cta = 2048;

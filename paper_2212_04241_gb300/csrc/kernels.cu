@@ -335,11 +335,127 @@ __host__ __device__ inline size_t collect_warp_smem(int cpt, int nm) {
          round16(sizeof(int32_t) * 32 * (size_t)nm);
 }
 
+// Per-warp shared memory of a clique's maps (the layout collect_warp_smem
+// sizes): per map its per-case value, its index-table offsets and message
+// row, and the map indices of 32 rows.
+template <int CPT>
+struct MapSmem {
+  float *mval;
+  int64_t *mA, *mB, *mrow;
+  int32_t *idx;
+  __device__ __forceinline__ MapSmem(unsigned char *ws, int max_maps) {
+    constexpr int W = 32 * CPT;
+    mval = reinterpret_cast<float *>(ws);
+    mA = reinterpret_cast<int64_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps));
+    mB = mA + max_maps;
+    mrow = mB + max_maps;
+    idx = reinterpret_cast<int32_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps) +
+                                      round16(3 * sizeof(int64_t) * (size_t)max_maps));
+  }
+};
+
+// Load clique C's maps [map_begin, map_begin + nmaps) into the warp's shared
+// memory.  Child maps gather rows of the child's message (scaled by 2^-k
+// per case); evidence maps keep each case's observed state: an entry whose
+// digit of the variable differs from it is zeroed (the 0/1 indicator of the
+// reduction step, evaluated instead of loaded).  Child maps come first.
+// Returns the number of child maps.
+template <int CPT>
+__device__ __forceinline__ int load_clique_maps(const DevPlan &P, const DevArena &A, const DClique &C, int nmaps,
+                                                int tile, const MapSmem<CPT> &sm, int lane) {
+  constexpr int W = 32 * CPT;
+  int nchild = 0;
+  for (int i = 0; i < nmaps; ++i) {
+    const DMap mp = P.maps[C.map_begin + i];
+    const bool child = mp.kind == MAP_CHILD;
+    if (lane == 0) {
+      sm.mA[i] = mp.A_off;
+      sm.mB[i] = mp.B_off;
+      sm.mrow[i] = child ? (A.phistar - A.psi) + ((int64_t)tile * P.sep_rows + mp.src_row) * W : 0;
+    }
+    nchild += child;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int c = col_of<CPT>(lane, k);
+      sm.mval[i * W + c] = child ? (P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]))
+                                              : 1.f)
+                                 : (float)A.ev[((int64_t)tile * P.n_vars + mp.src) * W + c];
+    }
+  }
+  __syncwarp();
+  return nchild;
+}
+
+// The clique table's rows r .. r+G-1 of a 32-row batch, per case: the base
+// entry (lane j holds row j's; a sliced plan gathers each case's slice
+// through fj and boff), times every child message row (gathered through the
+// batch's map indices, scaled by 2^-k), zeroed where an evidence map's
+// digit differs from the case's state -- the collect pass's reduction and
+// extension, in one fixed order (so a recomputed row equals the stored one
+// bit for bit).
+template <int CPT, int G, LoadMode MSG, bool SLICED>
+__device__ __forceinline__ void clique_rows(const DevArena &A, const MapSmem<CPT> &sm, const float *__restrict__ base,
+                                            const int32_t (&boff)[CPT], bool sliced, float bj, int32_t fj, int nchild,
+                                            int nm, int r, int nb, int lane, Vec<CPT> (&v)[G]) {
+  constexpr int W = 32 * CPT;
+  if (!sliced) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
+  } else {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int32_t f = __shfl_sync(kFull, fj, min(r + g, nb - 1));
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) v[g].x[k] = __ldg(base + f + boff[k]);
+    }
+  }
+  // child maps two at a time: both rows are requested before either is used
+  for (int i = 0; i < nchild; i += 2) {
+    const bool two = i + 1 < nchild;
+    const float *mp0 = A.psi + sm.mrow[i];
+    const float *mp1 = A.psi + sm.mrow[two ? i + 1 : i];
+    Vec<CPT> m0[G], m1[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) m0[g] = ldrow<CPT, MSG>(mp0 + (int64_t)sm.idx[i * 32 + min(r + g, nb - 1)] * W, lane);
+    if (two) {
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        m1[g] = ldrow<CPT, MSG>(mp1 + (int64_t)sm.idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
+    }
+    {
+      const Vec<CPT> sc = ldrow<CPT>(sm.mval + i * W, lane);
+#pragma unroll
+      for (int g = 0; g < G; ++g) vmul<CPT>(m0[g], sc);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) vmul<CPT>(v[g], m0[g]);
+    if (two) {
+      {
+        const Vec<CPT> sc = ldrow<CPT>(sm.mval + (i + 1) * W, lane);
+#pragma unroll
+        for (int g = 0; g < G; ++g) vmul<CPT>(m1[g], sc);
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) vmul<CPT>(v[g], m1[g]);
+    }
+  }
+  for (int i = nchild; i < nm; ++i) {  // evidence maps: idx is the variable's digit
+    const Vec<CPT> e = ldrow<CPT>(sm.mval + i * W, lane);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const float d = (float)sm.idx[i * 32 + min(r + g, nb - 1)];
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) v[g].x[k] = (e.x[k] < 0.f || e.x[k] == d) ? v[g].x[k] : 0.f;
+    }
+  }
+}
+
 // One collect work item (a warp's rows of one clique, one case tile).  MSG
 // is the load path of the children's messages: the read-only path when an
 // earlier kernel wrote them, coherent loads when warps of the same kernel
 // did (dataflow schedule).  SLICED instantiates the base-table gather of
 // plans specialised to an observed set; other plans compile without it.
+// A plan whose distribute pass recomputes the clique tables stores none.
 template <int CPT, LoadMode MSG, bool SLICED>
 __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
                                              unsigned char *ws, int max_maps, int lane) {
@@ -347,38 +463,10 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
   constexpr int G = kCollectGroup<CPT>;
   const DClique C = P.cl[it.task];
   const int nm = C.map_end - C.map_begin;
-  // ws: this warp's shared memory (16-byte aligned), collect_warp_smem bytes
-  float *mval = reinterpret_cast<float *>(ws);
-  int64_t *mA = reinterpret_cast<int64_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps));
-  int64_t *mB = mA + max_maps;
-  int64_t *mrow = mB + max_maps;
-  int32_t *idx = reinterpret_cast<int32_t *>(ws + round16(sizeof(float) * W * (size_t)max_maps) +
-                                             round16(3 * sizeof(int64_t) * (size_t)max_maps));
-
-  // Child maps gather rows of the child's message (scaled by 2^-k per case).
-  // Evidence maps keep each case's observed state: an entry whose digit of
-  // the variable differs from it is zeroed (the 0/1 indicator of the
-  // reduction step, evaluated instead of loaded).  Child maps come first.
+  const MapSmem<CPT> sm(ws, max_maps);
+  // the upward message's evidence maps follow the clique's maps
   const int nsev = C.sev_end - C.sev_begin;
-  int nchild = 0;
-  for (int i = 0; i < nm + nsev; ++i) {
-    const DMap mp = P.maps[C.map_begin + i];  // the upward message's evidence follows the maps
-    const bool child = mp.kind == MAP_CHILD;
-    if (lane == 0) {
-      mA[i] = mp.A_off;
-      mB[i] = mp.B_off;
-      mrow[i] = child ? (A.phistar - A.psi) + ((int64_t)tile * P.sep_rows + mp.src_row) * W : 0;
-    }
-    nchild += child;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-      const int c = col_of<CPT>(lane, k);
-      mval[i * W + c] = child ? (P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + mp.src) * W + c]))
-                                           : 1.f)
-                              : (float)A.ev[((int64_t)tile * P.n_vars + mp.src) * W + c];
-    }
-  }
-  __syncwarp();
+  const int nchild = load_clique_maps<CPT>(P, A, C, nm + nsev, tile, sm, lane);
   const int32_t R = (int32_t)C.R;
   const float *__restrict__ base = P.base32 + C.base_off;
   // sliced plan: each case reads the base-table slice of its observed-set
@@ -398,13 +486,14 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
   const int32_t *__restrict__ bB = P.ipool + C.bmap_B;
   float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
   float *phi_out = A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
+  const bool store = !P.recompute;
 
   // evidence entered into the upward message: entry s is zeroed for the
   // cases whose observed state of the variable differs from its digit at s
   auto sep_evidence = [&](int64_t s, Vec<CPT> &val) {
     for (int j = nm; j < nm + nsev; ++j) {
-      const float d = (float)__ldg(P.ipool + mA[j] + s);
-      const Vec<CPT> e = ldrow<CPT>(mval + j * W, lane);
+      const float d = (float)__ldg(P.ipool + sm.mA[j] + s);
+      const Vec<CPT> e = ldrow<CPT>(sm.mval + j * W, lane);
 #pragma unroll
       for (int k = 0; k < CPT; ++k) val.x[k] = (e.x[k] < 0.f || e.x[k] == d) ? val.x[k] : 0.f;
     }
@@ -421,65 +510,16 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
     const int32_t sj = (int32_t)ej / R, uj = (int32_t)ej - sj * R;  // |C| < 2^31
     const int32_t fj = sliced ? __ldg(bA + sj) + __ldg(bB + uj) : 0;  // base entry (sliced plan)
     const float bj = sliced ? 0.f : __ldg(base + ej);
-    for (int i = 0; i < nm; ++i) idx[i * 32 + lane] = __ldg(P.ipool + mA[i] + sj) + __ldg(P.ipool + mB[i] + uj);
+    for (int i = 0; i < nm; ++i) sm.idx[i * 32 + lane] = __ldg(P.ipool + sm.mA[i] + sj) + __ldg(P.ipool + sm.mB[i] + uj);
     const unsigned last = __ballot_sync(kFull, !it.split && uj == R - 1 && lane < nb);
     __syncwarp();
     for (int r = 0; r < nb; r += G) {
       Vec<CPT> v[G];
-      if (!sliced) {
-#pragma unroll
-        for (int g = 0; g < G; ++g) v[g] = vsplat<CPT>(__shfl_sync(kFull, bj, min(r + g, nb - 1)));
-      } else {
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const int32_t f = __shfl_sync(kFull, fj, min(r + g, nb - 1));
-#pragma unroll
-          for (int k = 0; k < CPT; ++k) v[g].x[k] = __ldg(base + f + boff[k]);
-        }
-      }
-      // child maps two at a time: both rows are requested before either is used
-      for (int i = 0; i < nchild; i += 2) {
-        const bool two = i + 1 < nchild;
-        const float *mp0 = A.psi + mrow[i];
-        const float *mp1 = A.psi + mrow[two ? i + 1 : i];
-        Vec<CPT> m0[G], m1[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) m0[g] = ldrow<CPT, MSG>(mp0 + (int64_t)idx[i * 32 + min(r + g, nb - 1)] * W, lane);
-        if (two) {
-#pragma unroll
-          for (int g = 0; g < G; ++g)
-            m1[g] = ldrow<CPT, MSG>(mp1 + (int64_t)idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
-        }
-        {
-          const Vec<CPT> sc = ldrow<CPT>(mval + i * W, lane);
-#pragma unroll
-          for (int g = 0; g < G; ++g) vmul<CPT>(m0[g], sc);
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) vmul<CPT>(v[g], m0[g]);
-        if (two) {
-          {
-            const Vec<CPT> sc = ldrow<CPT>(mval + (i + 1) * W, lane);
-#pragma unroll
-            for (int g = 0; g < G; ++g) vmul<CPT>(m1[g], sc);
-          }
-#pragma unroll
-          for (int g = 0; g < G; ++g) vmul<CPT>(v[g], m1[g]);
-        }
-      }
-      for (int i = nchild; i < nm; ++i) {  // evidence maps: idx is the variable's digit
-        const Vec<CPT> e = ldrow<CPT>(mval + i * W, lane);
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const float d = (float)idx[i * 32 + min(r + g, nb - 1)];
-#pragma unroll
-          for (int k = 0; k < CPT; ++k) v[g].x[k] = (e.x[k] < 0.f || e.x[k] == d) ? v[g].x[k] : 0.f;
-        }
-      }
+      clique_rows<CPT, G, MSG, SLICED>(A, sm, base, boff, sliced, bj, fj, nchild, nm, r, nb, lane, v);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         if (r + g < nb) {
-          strow<CPT, true>(psi + (e_first + b0 + r + g) * W, lane, v[g]);
+          if (store) strow<CPT, true>(psi + (e_first + b0 + r + g) * W, lane, v[g]);
           vadd<CPT>(part, v[g]);
           if ((last >> (r + g)) & 1u) {  // segment complete
             kahan_fold<CPT>(acc, comp, part);
@@ -529,13 +569,26 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect(DevPl
 // ---------------------------------------------------------------------------
 // One distribute work item (a warp's rows of one task, one case tile).  RHO
 // is the load path of the clique's ratio rows (see collect_item).
-template <int CPT, LoadMode RHO>
+// RECOMP: the plan stores no clique tables; a task reading the clique's
+// table recomputes each row it needs (clique_rows: the collect pass's
+// product, in its order) from the base table, the child messages and the
+// evidence, using the warp's shared memory `ws` for the clique's maps.
+template <int CPT, LoadMode RHO, bool RECOMP = false>
 __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
-                                                int lane) {
+                                                int lane, unsigned char *ws = nullptr) {
   constexpr int W = 32 * CPT;
-  constexpr int G = kDistGroup<CPT>;
+  constexpr int G = RECOMP ? kCollectGroup<CPT> : kDistGroup<CPT>;
   const DTask T = P.tasks[it.task];
   const DClique C = P.cl[T.clique];
+  const bool recomp = RECOMP && !T.src_sep;  // a separator's phi* rows are stored
+  MapSmem<CPT> sm(ws, RECOMP ? P.max_maps : 0);
+  const int nm = C.map_end - C.map_begin;
+  const int nchild = recomp ? load_clique_maps<CPT>(P, A, C, nm, tile, sm, lane) : 0;
+  const float *__restrict__ base = P.base32 + C.base_off;
+  const int32_t Rc = (int32_t)C.R;
+  int32_t no_off[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) no_off[k] = 0;
   // X rows: the clique's psi, or the phi* rows of its upward separator
   const float *psi = T.src_sep ? A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W
                                : A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
@@ -576,14 +629,25 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
     const int32_t ej = __ldg(At + tj) + __ldg(Bt + uj);
     const int32_t xj = root ? 0 : __ldg(sAt + tj) + __ldg(sBt + uj);
     const unsigned last = __ballot_sync(kFull, !it.split && uj == U - 1 && lane < nb);
+    float bj = 0.f;
+    if (recomp) {  // lane j: the base entry and map indices of its row's clique entry
+      const int32_t sj = ej / Rc, u2 = ej - sj * Rc;
+      bj = __ldg(base + ej);
+      for (int i = 0; i < nm; ++i) sm.idx[i * 32 + lane] = __ldg(P.ipool + sm.mA[i] + sj) + __ldg(P.ipool + sm.mB[i] + u2);
+      __syncwarp();
+    }
     for (int r = 0; r < nb; r += G) {
       Vec<CPT> p[G];
+      if (recomp) {
+        clique_rows<CPT, G, LD_NC, false>(A, sm, base, no_off, false, bj, 0, nchild, nm, r, nb, lane, p);
+      } else {
 #pragma unroll
-      for (int g = 0; g < G; ++g)
-        p[g] = ldrow<CPT, LD_STREAM>(psi + (int64_t)__shfl_sync(kFull, ej, min(r + g, nb - 1)) * W, lane);
+        for (int g = 0; g < G; ++g)
+          p[g] = ldrow<CPT, LD_STREAM>(psi + (int64_t)__shfl_sync(kFull, ej, min(r + g, nb - 1)) * W, lane);
+      }
       // the next group's rows are requested into L2 now: more bytes in
       // flight at the register-limited occupancy, without holding registers
-      if (r + G < nb) {
+      if (!recomp && r + G < nb) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
           const float *pa = psi + (int64_t)__shfl_sync(kFull, ej, min(r + G + g, nb - 1)) * W + lane * CPT;
@@ -615,6 +679,7 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
       }
       kahan_fold<CPT>(acc, comp, part);
     }
+    if (recomp) __syncwarp();  // the next batch rewrites the map indices
   }
   if (it.split) {
     Vec<CPT> tot;
@@ -811,21 +876,41 @@ __device__ __forceinline__ void distribute_unit(const DevPlan &P, const DevArena
   else distribute_item<CPT, RHO>(P, A, it, tile, lane);
 }
 
-// FUSED: the instantiation for plans whose work lists hold fused items;
-// plans without them run the plain item only, at the plain item's
-// register budget and occupancy.
-template <int CPT, bool FUSED>
-__global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocksPerSM : kDistributeBlocksPerSM)
+// Distribute kernel instantiations (MODE): kPlain for plans with stored
+// clique tables and no fused items, at the plain item's register budget
+// and occupancy; kFused for plans whose work lists hold fused items;
+// kRecomp for plans that recompute their clique tables (the collect
+// kernel's register budget and per-warp map memory).
+enum { kPlain = 0, kFused = 1, kRecomp = 2 };
+constexpr int dist_blocks_per_sm(int mode) {
+  return mode == kFused ? kFusedBlocksPerSM : mode == kRecomp ? kCollectBlocksPerSM : kDistributeBlocksPerSM;
+}
+
+// The warp's dynamic shared memory: fused secondary sums, or the clique's
+// maps when recomputing.
+template <int CPT, int MODE>
+__device__ __forceinline__ unsigned char *dist_warp_smem(const DevPlan &P, unsigned char *dsm, int warp) {
+  if constexpr (MODE == kFused) return dsm + (size_t)warp * P.sec_rows * (32 * CPT) * sizeof(float);
+  else if constexpr (MODE == kRecomp) return dsm + (size_t)warp * collect_warp_smem(CPT, P.max_maps);
+  else return dsm;
+}
+
+template <int CPT, int MODE, LoadMode RHO>
+__device__ __forceinline__ void dist_unit(const DevPlan &P, const DevArena &A, const DItem &it, int tile, int lane,
+                                          unsigned char *ws) {
+  if constexpr (MODE == kFused) distribute_unit<CPT, RHO>(P, A, it, tile, lane, reinterpret_cast<float *>(ws));
+  else if constexpr (MODE == kRecomp) distribute_item<CPT, RHO, true>(P, A, it, tile, lane, ws);
+  else distribute_item<CPT, RHO>(P, A, it, tile, lane);
+}
+
+template <int CPT, int MODE>
+__global__ void __launch_bounds__(kThreads, dist_blocks_per_sm(MODE))
     k_distribute(DevPlan P, DevArena A, int64_t item_begin, int64_t n_items) {
-  extern __shared__ __align__(16) float dsm[];
+  extern __shared__ __align__(16) unsigned char dsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t iw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (iw >= n_items) return;
-  if constexpr (FUSED)
-    distribute_unit<CPT, LD_NC>(P, A, P.ditems[item_begin + iw], blockIdx.y, lane,
-                                dsm + (size_t)warp * P.sec_rows * (32 * CPT));
-  else
-    distribute_item<CPT, LD_NC>(P, A, P.ditems[item_begin + iw], blockIdx.y, lane);
+  dist_unit<CPT, MODE, LD_NC>(P, A, P.ditems[item_begin + iw], blockIdx.y, lane, dist_warp_smem<CPT, MODE>(P, dsm, warp));
 }
 
 // ---------------------------------------------------------------------------
@@ -931,12 +1016,11 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect_flow(
   }
 }
 
-template <int CPT, bool FUSED>
-__global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocksPerSM : kDistributeBlocksPerSM)
-    k_distribute_flow(DevPlan P, DevArena A) {
-  extern __shared__ __align__(16) float dsm[];
+template <int CPT, int MODE>
+__global__ void __launch_bounds__(kThreads, dist_blocks_per_sm(MODE)) k_distribute_flow(DevPlan P, DevArena A) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   const int lane = threadIdx.x & 31;
-  float *sec = dsm + (size_t)(threadIdx.x >> 5) * P.sec_rows * (32 * CPT);
+  unsigned char *ws = dist_warp_smem<CPT, MODE>(P, dsm, threadIdx.x >> 5);
   int64_t item;
   int tile;
   while (next_unit(A.queue + 16, P.d_flow_pref, P.d_flow_begin, P.n_flow_layers, A.tiles, lane, item, tile)) {
@@ -944,12 +1028,10 @@ __global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocksPerSM : kDistrib
     const DTask &T = P.tasks[it.task];
     uint32_t *ready = A.ready + ((int64_t)tile * 2 + 1) * P.n_cliques;
     const uint32_t need = P.d_need[T.clique];
-    if (need == 0u || wait_ready(ready + T.clique, need, A.errflag, P.wait_limit_ns, lane)) {
-      if constexpr (FUSED) distribute_unit<CPT, LD_PLAIN>(P, A, it, tile, lane, sec);
-      else distribute_item<CPT, LD_PLAIN>(P, A, it, tile, lane);
-    }
+    if (need == 0u || wait_ready(ready + T.clique, need, A.errflag, P.wait_limit_ns, lane))
+      dist_unit<CPT, MODE, LD_PLAIN>(P, A, it, tile, lane, ws);
     // a fused item also completes its share of the secondary child's ratio
-    if (FUSED && it.fused && T.sec_kind == TASK_CHILD) {
+    if (MODE == kFused && it.fused && T.sec_kind == TASK_CHILD) {
       __threadfence();
       __syncwarp();
       if (lane == 0) atomicAdd(ready + T.sec_dst, 1u);
@@ -975,18 +1057,15 @@ __global__ void __launch_bounds__(kThreads, kCollectBlocksPerSM) k_collect_units
                                    smem_raw + (size_t)warp * collect_warp_smem(CPT, max_maps), max_maps, lane);
 }
 
-template <int CPT, bool FUSED>
-__global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocksPerSM : kDistributeBlocksPerSM)
+template <int CPT, int MODE>
+__global__ void __launch_bounds__(kThreads, dist_blocks_per_sm(MODE))
     k_distribute_units(DevPlan P, DevArena A, const int2 *units, int n_units) {
-  extern __shared__ __align__(16) float dsm[];
+  extern __shared__ __align__(16) unsigned char dsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (u >= n_units) return;
   const int2 un = units[u];
-  if constexpr (FUSED)
-    distribute_unit<CPT, LD_NC>(P, A, P.ditems[un.x], un.y, lane, dsm + (size_t)warp * P.sec_rows * (32 * CPT));
-  else
-    distribute_item<CPT, LD_NC>(P, A, P.ditems[un.x], un.y, lane);
+  dist_unit<CPT, MODE, LD_NC>(P, A, P.ditems[un.x], un.y, lane, dist_warp_smem<CPT, MODE>(P, dsm, warp));
 }
 
 // ---------------------------------------------------------------------------
@@ -1245,19 +1324,31 @@ size_t distribute_smem_bytes(int cpt, int sec_rows) {
   return (size_t)kWarps * (size_t)sec_rows * 32 * (size_t)cpt * sizeof(float);
 }
 
-// Calls f(CPT, FUSED) with both as compile-time constants.
+// Calls f(CPT, MODE) with both as compile-time constants.
 template <class F>
-static auto with_distribute(int cpt, bool fused, F &&f) {
+static auto with_distribute(int cpt, int mode, F &&f) {
   using std::integral_constant;
-  using yes = std::true_type;
-  using no = std::false_type;
-  if (cpt == 8) return fused ? f(integral_constant<int, 8>{}, yes{}) : f(integral_constant<int, 8>{}, no{});
-  if (cpt == 4) return fused ? f(integral_constant<int, 4>{}, yes{}) : f(integral_constant<int, 4>{}, no{});
-  if (cpt == 2) return fused ? f(integral_constant<int, 2>{}, yes{}) : f(integral_constant<int, 2>{}, no{});
-  return fused ? f(integral_constant<int, 1>{}, yes{}) : f(integral_constant<int, 1>{}, no{});
+  auto by_mode = [&](auto c) {
+    if (mode == kFused) return f(c, integral_constant<int, kFused>{});
+    if (mode == kRecomp) return f(c, integral_constant<int, kRecomp>{});
+    return f(c, integral_constant<int, kPlain>{});
+  };
+  if (cpt == 8) return by_mode(integral_constant<int, 8>{});
+  if (cpt == 4) return by_mode(integral_constant<int, 4>{});
+  if (cpt == 2) return by_mode(integral_constant<int, 2>{});
+  return by_mode(integral_constant<int, 1>{});
 }
 
-static bool has_fused(const DevPlan &P) { return P.fused_items > 0; }
+static int dist_mode(const DevPlan &P) {
+  return P.recompute ? kRecomp : P.fused_items > 0 ? kFused : kPlain;
+}
+
+// Dynamic shared memory of a distribute block in a mode.
+static size_t dist_smem(int cpt, int mode, int sec_rows, int max_maps) {
+  if (mode == kFused) return distribute_smem_bytes(cpt, sec_rows);
+  if (mode == kRecomp) return (size_t)kWarps * collect_warp_smem(cpt, max_maps);
+  return 0;
+}
 
 // Calls f(CPT, SLICED) with both as compile-time constants: the collect
 // kernels are instantiated per cases-per-thread and per plan kind.
@@ -1306,10 +1397,10 @@ void launch_distribute_units(int cpt, const DevPlan &P, const DevArena &A, const
                              cudaStream_t s) {
   if (n_units <= 0) return;
   const unsigned grid = (unsigned)((n_units + kWarps - 1) / kWarps);
-  const bool fu = has_fused(P);
-  const size_t sm = fu ? distribute_smem_bytes(cpt, P.sec_rows) : 0;
-  with_distribute(cpt, fu, [&](auto c, auto f) {
-    k_distribute_units<decltype(c)::value, decltype(f)::value><<<grid, kThreads, sm, s>>>(P, A, units, n_units);
+  const int mode = dist_mode(P);
+  const size_t sm = dist_smem(cpt, mode, P.sec_rows, P.max_maps);
+  with_distribute(cpt, mode, [&](auto c, auto m) {
+    k_distribute_units<decltype(c)::value, decltype(m)::value><<<grid, kThreads, sm, s>>>(P, A, units, n_units);
   });
 }
 
@@ -1327,29 +1418,34 @@ void launch_collect(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int
 
 
 
-cudaError_t configure_distribute_smem(int cpt, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return with_distribute(cpt, true, [&](auto c, auto fu) {
-    constexpr int CPT = decltype(c)::value;
-    constexpr bool FU = decltype(fu)::value;
-    cudaError_t e = cudaFuncSetAttribute((const void *)k_distribute<CPT, FU>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t configure_distribute_smem(int cpt, int sec_rows, int max_maps) {
+  for (int mode : {kFused, kRecomp}) {
+    const size_t bytes = dist_smem(cpt, mode, sec_rows, max_maps);
+    if (bytes <= 48 * 1024) continue;
+    const cudaError_t e = with_distribute(cpt, mode, [&](auto c, auto m) {
+      constexpr int CPT = decltype(c)::value;
+      constexpr int MODE = decltype(m)::value;
+      cudaError_t r = cudaFuncSetAttribute((const void *)k_distribute<CPT, MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (r != cudaSuccess) return r;
+      r = cudaFuncSetAttribute((const void *)k_distribute_units<CPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bytes);
+      if (r != cudaSuccess) return r;
+      return cudaFuncSetAttribute((const void *)k_distribute_flow<CPT, MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    });
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void *)k_distribute_units<CPT, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void *)k_distribute_flow<CPT, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes);
-  });
+  }
+  return cudaSuccess;
 }
 
 void launch_distribute(int cpt, const DevPlan &P, const DevArena &A, int64_t b, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   dim3 grid((unsigned)((n + kWarps - 1) / kWarps), (unsigned)A.tiles);
-  const bool fu = has_fused(P);
-  const size_t sm = fu ? distribute_smem_bytes(cpt, P.sec_rows) : 0;
-  with_distribute(cpt, fu, [&](auto c, auto f) {
-    k_distribute<decltype(c)::value, decltype(f)::value><<<grid, kThreads, sm, s>>>(P, A, b, n);
+  const int mode = dist_mode(P);
+  const size_t sm = dist_smem(cpt, mode, P.sec_rows, P.max_maps);
+  with_distribute(cpt, mode, [&](auto c, auto m) {
+    k_distribute<decltype(c)::value, decltype(m)::value><<<grid, kThreads, sm, s>>>(P, A, b, n);
   });
 }
 
@@ -1363,10 +1459,10 @@ void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int block
 }
 
 void launch_distribute_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, cudaStream_t s) {
-  const bool fu = has_fused(P);
-  const size_t sm = fu ? distribute_smem_bytes(cpt, P.sec_rows) : 0;
-  with_distribute(cpt, fu, [&](auto c, auto f) {
-    k_distribute_flow<decltype(c)::value, decltype(f)::value><<<blocks, kThreads, sm, s>>>(P, A);
+  const int mode = dist_mode(P);
+  const size_t sm = dist_smem(cpt, mode, P.sec_rows, P.max_maps);
+  with_distribute(cpt, mode, [&](auto c, auto m) {
+    k_distribute_flow<decltype(c)::value, decltype(m)::value><<<blocks, kThreads, sm, s>>>(P, A);
   });
 }
 
@@ -1381,20 +1477,23 @@ static int occupancy_of(K kernel, int threads, size_t smem) {
   return n > 0 ? n : 1;
 }
 
-int flow_blocks_per_sm(int cpt, bool collect, bool sliced, int max_maps, int sec_rows) {
-  if (collect) {
-    const int nw = collect_warps(cpt, max_maps);
-    const size_t smem = (size_t)nw * collect_warp_smem(cpt, max_maps);
-    return with_collect(cpt, sliced, [&](auto c, auto sl) {
-      return occupancy_of(k_collect_flow<decltype(c)::value, decltype(sl)::value>, 32 * nw, smem);
-    });
-  }
-  const bool fu = sec_rows > 0;
-  const size_t sm = fu ? distribute_smem_bytes(cpt, sec_rows) : 0;
-  return with_distribute(cpt, fu, [&](auto c, auto f) {
-    return occupancy_of(k_distribute_flow<decltype(c)::value, decltype(f)::value>, kThreads, sm);
+int flow_blocks_per_sm(int cpt, bool sliced, int max_maps) {
+  const int nw = collect_warps(cpt, max_maps);
+  const size_t smem = (size_t)nw * collect_warp_smem(cpt, max_maps);
+  return with_collect(cpt, sliced, [&](auto c, auto sl) {
+    return occupancy_of(k_collect_flow<decltype(c)::value, decltype(sl)::value>, 32 * nw, smem);
   });
 }
+
+int distribute_flow_blocks_per_sm(int cpt, const DevPlan &P) {
+  const int mode = dist_mode(P);
+  const size_t sm = dist_smem(cpt, mode, P.sec_rows, P.max_maps);
+  return with_distribute(cpt, mode, [&](auto c, auto m) {
+    return occupancy_of(k_distribute_flow<decltype(c)::value, decltype(m)::value>, kThreads, sm);
+  });
+}
+
+size_t recompute_warp_smem_bytes(int cpt, int max_maps) { return collect_warp_smem(cpt, max_maps); }
 
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,
                        const int32_t *d_ev, cudaStream_t s) {

@@ -48,6 +48,8 @@ struct DevPlan {
   int32_t n_cliques;
   int32_t root;
   int32_t rescale;           // 1: messages scaled by 2^-k (k per case and message)
+  int32_t recompute;         // 1: no stored clique tables; the distribute pass recomputes them
+  int32_t max_maps;          // most maps of a clique (the warp's shared-memory map layout)
   int32_t sec_rows;          // shared-memory rows (W floats) per warp of the distribute kernels (fused pairs)
   int64_t fused_items;       // fused items in the work lists (0: the plain distribute kernels)
   int64_t psi_rows;          // rows of one tile's psi region (sum |C|)
@@ -111,8 +113,9 @@ constexpr int kMaxTilesPerChunk = 16384;
 // dataflow schedule: one persistent launch per pass (blocks = SMs x resident blocks per SM)
 void launch_collect_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, int max_maps, cudaStream_t s);
 void launch_distribute_flow(int cpt, const DevPlan &P, const DevArena &A, int blocks, cudaStream_t s);
-// (distribute: sec_rows > 0 selects the kernels of plans with fused items)
-int flow_blocks_per_sm(int cpt, bool collect, bool sliced, int max_maps, int sec_rows = 0);
+int flow_blocks_per_sm(int cpt, bool sliced, int max_maps);  // the collect pass
+// the distribute pass, in the plan's mode (plain, fused items, recomputed tables)
+int distribute_flow_blocks_per_sm(int cpt, const DevPlan &P);
 // explicit (item, tile) unit lists: one launch per pass over tiles at
 // different layers (iteration-level batching of the serving loop)
 void launch_collect_units(int cpt, const DevPlan &P, const DevArena &A, const int2 *units, int n_units, int max_maps,
@@ -121,7 +124,9 @@ void launch_distribute_units(int cpt, const DevPlan &P, const DevArena &A, const
                              cudaStream_t s);
 // dynamic shared memory of a distribute block (fused pairs' secondary sums)
 size_t distribute_smem_bytes(int cpt, int sec_rows);
-cudaError_t configure_distribute_smem(int cpt, size_t bytes);
+// a warp's shared memory for a clique's maps when recomputing its rows
+size_t recompute_warp_smem_bytes(int cpt, int max_maps);
+cudaError_t configure_distribute_smem(int cpt, int sec_rows, int max_maps);
 
 // plain FP64 path
 void launch_plain_init(double *psi, const double *base, const DPlainMap &m, const int64_t *pool,

@@ -39,7 +39,7 @@ class CompileOpts(ctypes.Structure):
                 ("rescale", ctypes.c_int32), ("n_query_set", ctypes.c_int32), ("query_set", ctypes.c_void_p),
                 ("collect_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
                 ("distribute_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
-                ("fuse_distribute", ctypes.c_int32)]
+                ("fuse_distribute", ctypes.c_int32), ("recompute_psi", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -179,7 +179,8 @@ def autotune(net, n_cases: int, **opts):
                            int(n_cases), ctypes.byref(best), ctypes.byref(ns)))
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
                                            "items_per_tile_distribute", "use_graphs", "arena_bytes",
-                                           "max_clique_entries", "schedule", "rescale", "fuse_distribute")}
+                                           "max_clique_entries", "schedule", "rescale", "fuse_distribute",
+                                           "recompute_psi")}
     for k in ("collect_rows_by_bucket", "distribute_rows_by_bucket"):
         out[k] = [int(x) for x in getattr(best, k)]
     for k in ("observed_set", "query_set"):
