@@ -606,14 +606,20 @@ def main():
     # algorithmic bytes of one pass per kernel kind (per case):
     #   collect:    psi written 4|C|, messages written 4|S| and read 4|S|
     #   distribute: psi read 4|C|, ratios written 4|S| and read 4|S|
-    per_case = 4.0 * info["sum_clique_entries"] + 8.0 * info["sum_sep_entries"]
-    bytes_dom = per_case * n_cases
+    # with recomputed clique tables no psi moves: collect writes and the
+    # parent reads the messages (8|S|); distribute reads the child messages
+    # once more (4|S|) and writes and reads the ratios (8|S|)
+    recompute = bool(int(tuned.get("recompute_psi", 0))) and not observed_set
+    C, S = float(info["sum_clique_entries"]), float(info["sum_sep_entries"])
+    per_case_kind = ({"collect": 8.0 * S, "distribute": 12.0 * S} if recompute else
+                     {"collect": 4.0 * C + 8.0 * S, "distribute": 4.0 * C + 8.0 * S})
+    bytes_dom = per_case_kind[dom] * n_cases
     achieved = bytes_dom / (kinds[dom] / 1e3) / 1e9
+    other = "collect" if dom == "distribute" else "distribute"
+    other_frac = per_case_kind[other] * n_cases / (kinds[other] / 1e3)
     peak, peak_src = _peaks()
     dataflow = int(tuned.get("schedule", J.JT_SCHEDULE_DATAFLOW)) == J.JT_SCHEDULE_DATAFLOW
     kernel = f"k_{dom}_flow" if dataflow else f"k_{dom}"
-    # the plan's distribute work-item target (0 in the options = items_per_tile, whose 0 = 192)
-    items_d = int(tuned.get("items_per_tile_distribute") or tuned.get("items_per_tile") or 192)
     ksha = _kernel_source_hash()
     traffic = (MEASURED_TRAFFIC.get((name, n_cases, _distribute_shape(tuned), ksha))
                if dataflow and dom == "distribute" and not observed_set else None)
@@ -624,7 +630,11 @@ def main():
                                    f"kernel source sha256 {ksha}" if traffic is not None else
                                    f"no stored ncu capture for kernel source sha256 {ksha} and this plan shape"),
                 "launches": prof[f"{dom}_launches"],
-                "kernel_ms_per_pass": kinds[dom], "other_kernel_ms_per_pass": kinds["collect" if dom == "distribute" else "distribute"],
+                "kernel_ms_per_pass": kinds[dom], "other_kernel_ms_per_pass": kinds[other],
+                "algorithmic_bytes_per_case": per_case_kind[dom],
+                "tables": "recomputed in the distribute pass" if recompute else "stored by the collect pass",
+                "other_kernel": (f"k_{other}_flow" if dataflow else f"k_{other}"),
+                "other_kernel_frac": other_frac / 1e9 / peak,
                 "whole_pass_algorithmic_GBps": info["algorithmic_bytes_per_case"] * n_cases / (prof["total_ms"] / 1e3) / 1e9}
 
     # end to end through jt_infer with host buffers

@@ -766,6 +766,18 @@ __device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const De
     }
   };
 
+  // the divisor rows (phi*) of an F-block's secondary targets are requested
+  // into L2 when the F-block starts, so that its flush finds them there
+  auto prefetch_sec = [&](int64_t fb) {
+    const DTask &Tt = P.tasks[it.task];
+    if (Tt.sec_kind != TASK_CHILD) return;
+    constexpr int kLines = W * 4 / 128;  // 128-byte lines per row
+    for (int j = lane; j < nb2 * kLines; j += 32) {
+      const float *pa = A.phistar + ((int64_t)tile * P.sep_rows + sec_row(fb, j / kLines)) * W + (j % kLines) * 32;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+    }
+  };
+  prefetch_sec(it.t0 / a);
   const int32_t t_first = (int32_t)it.t0;
   const int32_t count = (int32_t)(it.nt * (int64_t)U);
   Vec<CPT> acc = vzero<CPT>(), comp = vzero<CPT>(), part = vzero<CPT>();
@@ -832,6 +844,7 @@ __device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const De
           if ((fend >> (r + g)) & 1u) {  // F-block complete: its secondary targets
             const int64_t fb = __shfl_sync(kFull, tj, r + g) / a;
             flush_sec(fb);
+            if ((fb + 1) * a < (int64_t)it.t0 + it.nt) prefetch_sec(fb + 1);
           }
         }
       }
@@ -852,17 +865,21 @@ __device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const De
       __threadfence();
       const int64_t fb = it.t0 / a;
       const int first = it.partial - it.piece * nb2;
-      const int kind2 = P.tasks[it.task].sec_kind;
-      for (int k = 0; k < nb2; ++k) {
-        Vec<CPT> tot = vzero<CPT>();
-        for (int q = 0; q < it.npieces; ++q) {
+      // sum in piece order into the shared-memory rows (the loads of one
+      // piece's rows are independent and issued together), then write the
+      // targets as an F-block flush does
+      for (int q = 0; q < it.npieces; ++q) {
+#pragma unroll 4
+        for (int k = 0; k < nb2; ++k) {
           const Vec<CPT> x =
               ldrow<CPT, LD_CG>(A.partial + ((int64_t)tile * P.n_partials + first + q * nb2 + k) * W, lane);
+          Vec<CPT> t = q == 0 ? vzero<CPT>() : ldrow<CPT>(sec + (int64_t)k * W, lane);
 #pragma unroll
-          for (int c = 0; c < CPT; ++c) tot.x[c] += x.x[c];
+          for (int c = 0; c < CPT; ++c) t.x[c] += x.x[c];
+          strow<CPT>(sec + (int64_t)k * W, lane, t);
         }
-        write(kind2, sec_row(fb, k), tot);
       }
+      flush_sec(fb);
       if (lane == 0) A.counters[(int64_t)tile * P.n_groups + it.group] = 0u;
     }
   }
