@@ -228,6 +228,12 @@ typedef struct {
                                  distribute pairs are not used with it;
                                  ignored for plans specialised to an
                                  observed set.  0 (default): stored. */
+  int32_t collect_prefetch;   /* 1: the collect pass requests each child
+                                 message's rows of the next row group into
+                                 L2 while it multiplies the current group
+                                 (helps where the messages do not fit L2,
+                                 costs instructions elsewhere); 0 (default):
+                                 off.  jt_autotune tries it per plan. */
 } jt_compile_opts;
 
 typedef struct {
@@ -411,9 +417,9 @@ JT_API jt_status jt_profile(jt_plan *plan, int32_t n_cases, const int32_t *d_evi
  *      the tile shape rows x cases -- over the powers of two 32 .. 4096,
  *      each pass keeping its own best value (coordinate descent; a change
  *      is kept when it is at least 1 % faster);
- *   3. the result with fuse_distribute turned the other way, and with
- *      recompute_psi turned the other way (each recompiled), the fastest
- *      kept if it is at least 1 % faster.
+ *   3. the result with fuse_distribute, recompute_psi and collect_prefetch
+ *      each turned the other way (each recompiled), the fastest kept if it
+ *      is at least 1 % faster.
  * Between the candidates of stages 1 and 2 only the work lists are
  * rebuilt, not the plan.
  * Writes the result to *best (base fields kept; the bucket tables in

@@ -372,6 +372,7 @@ static jt_status upload_plan(jt_plan *pl) {
   D.n_nan_cols = (int32_t)P.io_nan_cols.size();
   D.sec_rows = P.sec_rows;
   D.recompute = P.recompute;
+  D.msg_prefetch = P.opts.collect_prefetch ? 1 : 0;
   int max_maps = 0;
   for (const Level &lv : P.levels) max_maps = std::max(max_maps, lv.c_max_maps);
   D.max_maps = max_maps;
@@ -1136,13 +1137,11 @@ static jt_status jt_autotune_impl(int32_t n_vars, const int32_t *card, const int
   // per SM), and with recomputed clique tables; which one wins depends on
   // the network
   if (result == JT_OK && best_cw > 0) {
-    jt_compile_opts alts[2] = {best_o, best_o};
+    jt_compile_opts alts[3] = {best_o, best_o, best_o};
     alts[0].fuse_distribute = best_o.fuse_distribute ? 0 : 1;
     alts[1].recompute_psi = best_o.recompute_psi ? 0 : 1;
-    const jt_compile_opts base_best = best_o;
-    for (const jt_compile_opts &alt0 : alts) {
-      jt_compile_opts alt = alt0;
-      if (&alt0 == &alts[1]) alt.fuse_distribute = base_best.fuse_distribute;
+    alts[2].collect_prefetch = best_o.collect_prefetch ? 0 : 1;
+    for (const jt_compile_opts &alt : alts) {
       jt_plan *pl = nullptr;
       jt_status st = jt_compile(n_vars, card, parent_ptr, parents, cpt, &alt, &pl);
       double c_ms = -1, d_ms = -1;

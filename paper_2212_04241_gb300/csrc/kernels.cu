@@ -393,10 +393,12 @@ __device__ __forceinline__ int load_clique_maps(const DevPlan &P, const DevArena
 // digit differs from the case's state -- the collect pass's reduction and
 // extension, in one fixed order (so a recomputed row equals the stored one
 // bit for bit).
+// prefetch: the next group's rows of every child message are requested into
+// L2 after this group's loads.
 template <int CPT, int G, LoadMode MSG, bool SLICED>
 __device__ __forceinline__ void clique_rows(const DevArena &A, const MapSmem<CPT> &sm, const float *__restrict__ base,
                                             const int32_t (&boff)[CPT], bool sliced, float bj, int32_t fj, int nchild,
-                                            int nm, int r, int nb, int lane, Vec<CPT> (&v)[G]) {
+                                            int nm, int r, int nb, int lane, bool prefetch, Vec<CPT> (&v)[G]) {
   constexpr int W = 32 * CPT;
   if (!sliced) {
 #pragma unroll
@@ -421,6 +423,15 @@ __device__ __forceinline__ void clique_rows(const DevArena &A, const MapSmem<CPT
 #pragma unroll
       for (int g = 0; g < G; ++g)
         m1[g] = ldrow<CPT, MSG>(mp1 + (int64_t)sm.idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
+    }
+    if (prefetch && r + G < nb) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(mp0 + (int64_t)sm.idx[i * 32 + min(r + G + g, nb - 1)] * W + lane * CPT));
+        if (two)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(mp1 + (int64_t)sm.idx[(i + 1) * 32 + min(r + G + g, nb - 1)] * W +
+                                                          lane * CPT));
+      }
     }
     {
       const Vec<CPT> sc = ldrow<CPT>(sm.mval + i * W, lane);
@@ -515,7 +526,7 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
     __syncwarp();
     for (int r = 0; r < nb; r += G) {
       Vec<CPT> v[G];
-      clique_rows<CPT, G, MSG, SLICED>(A, sm, base, boff, sliced, bj, fj, nchild, nm, r, nb, lane, v);
+      clique_rows<CPT, G, MSG, SLICED>(A, sm, base, boff, sliced, bj, fj, nchild, nm, r, nb, lane, P.msg_prefetch != 0, v);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         if (r + g < nb) {
@@ -639,7 +650,7 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
     for (int r = 0; r < nb; r += G) {
       Vec<CPT> p[G];
       if (recomp) {
-        clique_rows<CPT, G, LD_NC, false>(A, sm, base, no_off, false, bj, 0, nchild, nm, r, nb, lane, p);
+        clique_rows<CPT, G, LD_NC, false>(A, sm, base, no_off, false, bj, 0, nchild, nm, r, nb, lane, false, p);
       } else {
 #pragma unroll
         for (int g = 0; g < G; ++g)

@@ -39,7 +39,8 @@ class CompileOpts(ctypes.Structure):
                 ("rescale", ctypes.c_int32), ("n_query_set", ctypes.c_int32), ("query_set", ctypes.c_void_p),
                 ("collect_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
                 ("distribute_rows_by_bucket", ctypes.c_int32 * JT_SIZE_BUCKETS),
-                ("fuse_distribute", ctypes.c_int32), ("recompute_psi", ctypes.c_int32)]
+                ("fuse_distribute", ctypes.c_int32), ("recompute_psi", ctypes.c_int32),
+                ("collect_prefetch", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -180,7 +181,7 @@ def autotune(net, n_cases: int, **opts):
     out = {k: getattr(best, k) for k in ("root_rule", "cases_per_thread", "rows_per_cta", "items_per_tile",
                                            "items_per_tile_distribute", "use_graphs", "arena_bytes",
                                            "max_clique_entries", "schedule", "rescale", "fuse_distribute",
-                                           "recompute_psi")}
+                                           "recompute_psi", "collect_prefetch")}
     for k in ("collect_rows_by_bucket", "distribute_rows_by_bucket"):
         out[k] = [int(x) for x in getattr(best, k)]
     for k in ("observed_set", "query_set"):

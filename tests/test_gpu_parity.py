@@ -402,3 +402,15 @@ def test_recomputed_tables_equal_stored_bitwise(name, n_cases, schedule):
     assert recomp.info()["arena_bytes"] < stored.info()["arena_bytes"]
     idx = np.arange(min(n_cases, 24))
     assert_parity32(b[0][idx], b[1][idx], b[2][idx], *_oracle(net, ev[idx]), where=f"recompute {name}")
+
+
+@pytest.mark.parametrize("name,n_cases", [("bn60", 1000), ("bn420", 128)])
+def test_collect_prefetch_changes_no_result(name, n_cases):
+    """collect_prefetch only requests rows into L2 ahead of use: outputs are
+    bit for bit those of the plan without it."""
+    net = configs.network(name)
+    ev = configs.evidence(name, net, n_cases=n_cases, seed=56)
+    a = _device_run(J.Plan(net), ev)
+    b = _device_run(J.Plan(net, collect_prefetch=1), ev)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y, equal_nan=True)
