@@ -494,7 +494,8 @@ JT_API jt_status jt_server_add_plan(jt_server *srv, jt_plan *plan, int32_t *plan
  * kernels -- and one tick is two launches over every active tile, each at
  * its own layer.  A request arriving while other tiles are mid-pass starts
  * at the next tick, in a free tile, instead of waiting for a whole pass.
- * At most two ticks of a plan are in flight; they run on a stream of the
+ * Up to eight ticks of a plan are enqueued ahead (phases advance on the
+ * host), so ticks run back to back; they run on a stream of the
  * highest priority, so their blocks are dispatched ahead of the batch
  * slots' passes.  Results are the same bit for
  * bit as the batch-slot path's (same kernels per tile, fixed per-case

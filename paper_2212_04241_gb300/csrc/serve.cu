@@ -79,26 +79,31 @@ struct Io {
 // root, then its finalize kernels.  A tick is two launches over explicit
 // (work item, tile) lists -- every active tile's units at that tile's own
 // layer -- so a tile admitted now joins the passes of tiles admitted
-// earlier at the next tick instead of waiting for them to finish.  At most
-// two ticks are in flight; a tile's results are handed back when the tick
-// that finalized it has completed.
+// earlier at the next tick instead of waiting for them to finish.  A tile's
+// phase advances on the host, independent of the GPU's progress, so up to
+// kRollDepth ticks are enqueued ahead (each with its own unit-list buffers
+// and completion event): the ticks run back to back on the GPU without a
+// host round trip between them, and a request arriving meanwhile joins at
+// the next tick the host enqueues.  A tile's results are handed back when
+// the tick that finalized it has completed.
 struct RollTile {
   int phase = -1;            // -1 free; 0..2H+1 the next layer step; kDone finalized
   int64_t done_tick = -1;    // the tick whose completion makes its results readable
   std::vector<Request> reqs;
 };
 constexpr int kDone = 1 << 30;
+constexpr int kRollDepth = 8;  // ticks of one plan enqueued ahead of the GPU
 
 struct Roll {
   size_t off = 0, bytes = 0;   // pool region of the tiles' tables
   jt::Arena arena;
   int R = 0;                   // tiles
   cudaStream_t stream = nullptr;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t ev[kRollDepth] = {};
   std::vector<RollTile> tiles;
   void *d_io = nullptr, *h_io = nullptr;  // per tile: evidence, log P(e), posteriors, status
   size_t io_tile = 0, o_lp = 0, o_post = 0, o_st = 0;
-  int2 *d_units = nullptr, *h_units = nullptr;  // [tick parity][pass][cap]
+  int2 *d_units = nullptr, *h_units = nullptr;  // [tick % kRollDepth][pass][cap]
   size_t cap = 0;
   int64_t ticks = 0;
   std::deque<int64_t> outstanding;  // enqueued ticks not yet seen complete
@@ -368,7 +373,7 @@ void roll_tick(jt_server *S, int pid) {
   const Plan &P = pl->P;
   const int W = P.tile, H = P.height;
   const int64_t k = r.ticks++;
-  const int par = (int)(k & 1);
+  const int par = (int)(k % kRollDepth);
   cudaStream_t st_ = r.stream;
   std::lock_guard<std::mutex> plk(pl->mu);
   // admissions
@@ -442,7 +447,7 @@ void roll_tick(jt_server *S, int pid) {
   r.outstanding.push_back(k);
 }
 
-// Retire completed ticks and enqueue the next one of every rolling plan.
+// Retire completed ticks and enqueue the next ones of every rolling plan.
 bool roll_step(jt_server *S) {
   bool progress = false;
   for (size_t pid = 0; pid < S->plans.size(); ++pid) {
@@ -451,20 +456,21 @@ bool roll_step(jt_server *S) {
     Roll &r = *pe.roll;
     while (!r.outstanding.empty()) {
       const int64_t k = r.outstanding.front();
-      const cudaError_t q = cudaEventQuery(r.ev[k & 1]);
+      const cudaError_t q = cudaEventQuery(r.ev[k % kRollDepth]);
       if (q == cudaErrorNotReady) break;
       if (q != cudaSuccess) cudaGetLastError();
       r.outstanding.pop_front();
       roll_retire(S, (int)pid, k);
       progress = true;
     }
-    if (r.outstanding.size() >= 2) continue;  // its unit buffers are still in use
-    bool active = false, free_tile = false;
-    for (const RollTile &T : r.tiles) {
-      active = active || (T.phase >= 0 && T.phase != kDone);
-      free_tile = free_tile || T.phase == -1;
-    }
-    if (active || (free_tile && !pe.pending.empty())) {
+    // enqueue ticks while a unit buffer is free and there is work
+    while (r.outstanding.size() < (size_t)kRollDepth) {
+      bool active = false, free_tile = false;
+      for (const RollTile &T : r.tiles) {
+        active = active || (T.phase >= 0 && T.phase != kDone);
+        free_tile = free_tile || T.phase == -1;
+      }
+      if (!active && !(free_tile && !pe.pending.empty())) break;
       roll_tick(S, (int)pid);
       progress = true;
     }
@@ -680,16 +686,17 @@ static jt_status jt_server_add_plan_rolling_impl(jt_server *S, jt_plan *pl, int3
   // large plan
   int least = 0, greatest = 0;
   cudaDeviceGetStreamPriorityRange(&least, &greatest);
-  if (cudaStreamCreateWithPriority(&r->stream, cudaStreamNonBlocking, greatest) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->ev[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithPriority(&r->stream, cudaStreamNonBlocking, greatest) == cudaSuccess;
+  for (int i = 0; ok && i < kRollDepth; ++i)
+    ok = cudaEventCreateWithFlags(&r->ev[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
     return fail(JT_ECUDA, "rolling plan: stream or events");
   }
   if (cudaMalloc(&r->d_io, r->io_tile * tiles) != cudaSuccess ||
       cudaHostAlloc(&r->h_io, r->io_tile * tiles, cudaHostAllocDefault) != cudaSuccess ||
-      cudaMalloc((void **)&r->d_units, sizeof(int2) * 4 * r->cap) != cudaSuccess ||
-      cudaHostAlloc((void **)&r->h_units, sizeof(int2) * 4 * r->cap, cudaHostAllocDefault) != cudaSuccess) {
+      cudaMalloc((void **)&r->d_units, sizeof(int2) * 2 * kRollDepth * r->cap) != cudaSuccess ||
+      cudaHostAlloc((void **)&r->h_units, sizeof(int2) * 2 * kRollDepth * r->cap, cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     return fail(JT_ENOMEM, "rolling plan: staging buffers");
   }
