@@ -44,17 +44,13 @@ template <int CPT>
 constexpr int kCollectGroup = CPT >= 8 ? 2 : 4;
 template <int CPT>
 constexpr int kDistGroup = CPT >= 8 ? 2 : 4;
-// rows per group of the fused distribute item (its kernel runs at three
-// blocks per SM, with the registers for four rows)
-template <int CPT>
-constexpr int kFusedGroup = CPT >= 8 ? 2 : 4;
 // Resident blocks per SM the register allocation aims at: the collect
 // kernel keeps its row group in registers without spilling at 2; the
 // distribute kernel streams psi and gains from more warps in flight.
 constexpr int kCollectBlocksPerSM = 2;
 constexpr int kDistributeBlocksPerSM = 4;
-// the distribute kernels of plans with fused pairs carry both item kinds
-// and need more registers: three blocks per SM
+// the distribute kernels of plans with fused pairs run both item kinds in
+// one row loop, at the plain kernel's occupancy
 constexpr int kFusedBlocksPerSM = 3;
 
 // CPT cases of one thread inside a row of W = 32*CPT cases.  For CPT >= 4
@@ -589,8 +585,8 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
                                                 int lane, unsigned char *ws = nullptr) {
   constexpr int W = 32 * CPT;
   constexpr int G = RECOMP ? kCollectGroup<CPT> : kDistGroup<CPT>;
-  const DTask T = P.tasks[it.task];
-  const DClique C = P.cl[T.clique];
+  const DTask &T = P.tasks[it.task];
+  const DClique &C = P.cl[T.clique];
   const bool recomp = RECOMP && !T.src_sep;  // a separator's phi* rows are stored
   MapSmem<CPT> sm(ws, RECOMP ? P.max_maps : 0);
   const int nm = C.map_end - C.map_begin;
@@ -605,15 +601,16 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
                                : A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
   const float *rho = A.rho + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
   const bool root = !T.src_sep && C.is_root != 0;
-  Vec<CPT> rs;
+  // a component root's scale 2^-k per case (computed where it is used, so
+  // that it holds no registers through the row loop)
+  auto root_scale = [&]() {
+    Vec<CPT> rs;
 #pragma unroll
-  for (int k = 0; k < CPT; ++k)
-    rs.x[k] = root && P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + col_of<CPT>(lane, k)]))
-                   : 1.f;
-  const int32_t *__restrict__ At = P.ipool + T.A_off;
-  const int32_t *__restrict__ sAt = P.ipool + T.sA_off;
-  const int32_t *__restrict__ Bt = P.ipool + T.B_off;
-  const int32_t *__restrict__ sBt = P.ipool + T.sB_off;
+    for (int k = 0; k < CPT; ++k)
+      rs.x[k] = P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + col_of<CPT>(lane, k)]))
+                          : 1.f;
+    return rs;
+  };
   const int32_t U = (int32_t)T.U;
 
   auto output = [&](int64_t t, const Vec<CPT> &val) {
@@ -637,8 +634,10 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
     // lane j: indices of row b0 + j, rows flattened as (t, u)
     const int32_t f = u_first + b0 + min(lane, nb - 1);
     const int32_t tj = t_first + f / U, uj = f - (f / U) * U;
-    const int32_t ej = __ldg(At + tj) + __ldg(Bt + uj);
-    const int32_t xj = root ? 0 : __ldg(sAt + tj) + __ldg(sBt + uj);
+    // the index tables are read through the task (no pointers held across
+    // the row loop)
+    const int32_t ej = __ldg(P.ipool + T.A_off + tj) + __ldg(P.ipool + T.B_off + uj);
+    const int32_t xj = root ? 0 : __ldg(P.ipool + T.sA_off + tj) + __ldg(P.ipool + T.sB_off + uj);
     const unsigned last = __ballot_sync(kFull, !it.split && uj == U - 1 && lane < nb);
     float bj = 0.f;
     if (recomp) {  // lane j: the base entry and map indices of its row's clique entry
@@ -673,6 +672,7 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
 #pragma unroll
         for (int g = 0; g < G; ++g) vmul<CPT>(p[g], q[g]);
       } else {
+        const Vec<CPT> rs = root_scale();
 #pragma unroll
         for (int g = 0; g < G; ++g) vmul<CPT>(p[g], rs);
       }
@@ -698,35 +698,42 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
   }
 }
 
-// One fused distribute work item (see DTask): whole primary targets
-// [t0, t0 + nt) of one F-block, or whole F-blocks.  Every row is read once:
-// the primary target's sum runs in registers (as in distribute_item), the
-// secondary targets of the F-block are summed in this warp's shared memory
-// (sec_b rows of W floats, each lane its own CPT columns, so no two lanes
-// touch the same word) and written when the F-block ends -- or, for a
-// piece of an F-block, written as partial sums that the last piece to
-// finish adds in piece order.
+// The work item of a plan with fused pairs: a single task's item (as
+// distribute_item), or a fused pair's item (see DTask): whole primary
+// targets [t0, t0 + nt) of one F-block, or whole F-blocks.  Both kinds run
+// the same row loop.  In a fused item every row is read once: the primary
+// target's sum runs in registers, the secondary targets of the F-block are
+// summed in this warp's shared memory (sec_b rows of W floats, each lane
+// its own CPT columns, so no two lanes touch the same word).  The 32-row
+// batches of a fused item restart at every F-block, so an F-block ends with
+// a batch and its secondary targets are written between batches, outside
+// the loop that holds the rows in flight; a piece of an F-block writes its
+// secondary sums as partials that the last piece to finish adds in piece
+// order.
 template <int CPT, LoadMode RHO>
-__device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
-                                                      int lane, float *sec) {
+__device__ __forceinline__ void distribute_pair_item(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
+                                                     int lane, float *sec) {
   constexpr int W = 32 * CPT;
-  constexpr int G = kFusedGroup<CPT>;
+  constexpr int G = kDistGroup<CPT>;
   const DTask &T = P.tasks[it.task];
-  const DClique C = P.cl[T.clique];
-  const float *psi = A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
+  const DClique &C = P.cl[T.clique];
+  const bool fz = it.fused != 0;
+  const float *psi = T.src_sep ? A.phistar + ((int64_t)tile * P.sep_rows + C.sep_row) * W
+                               : A.psi + ((int64_t)tile * P.psi_rows + C.psi_row) * W;
   const float *rho = A.rho + ((int64_t)tile * P.sep_rows + C.sep_row) * W;
-  const bool root = C.is_root != 0;
-  Vec<CPT> rs;
+  const bool root = !T.src_sep && C.is_root != 0;
+  // a component root's scale 2^-k per case (computed where it is used, so
+  // that it holds no registers through the row loop)
+  auto root_scale = [&]() {
+    Vec<CPT> rs;
 #pragma unroll
-  for (int k = 0; k < CPT; ++k)
-    rs.x[k] = root && P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + col_of<CPT>(lane, k)]))
-                   : 1.f;
-  const int32_t *__restrict__ At = P.ipool + T.fA_off;
-  const int32_t *__restrict__ sAt = P.ipool + T.fsA_off;
-  const int32_t *__restrict__ Bt = P.ipool + T.fB_off;
-  const int32_t *__restrict__ sBt = P.ipool + T.fsB_off;
-  const int32_t *__restrict__ Ku = P.ipool + T.ku_off;
-  const int32_t U = (int32_t)T.U, a = T.sec_a, nb2 = T.sec_b;
+    for (int k = 0; k < CPT; ++k)
+      rs.x[k] = P.rescale ? pow2f(-pow2_exp(A.maxbits[((int64_t)tile * P.n_cliques + T.clique) * W + col_of<CPT>(lane, k)]))
+                          : 1.f;
+    return rs;
+  };
+  const int32_t U = (int32_t)T.U;
+  const int32_t a = fz ? T.sec_a : 1, nb2 = fz ? T.sec_b : 0;
 
   // a target's value: a separator ratio (0/0 := 0) or a posterior marginal
   auto write = [&](int kind, int64_t row, const Vec<CPT> &val) {
@@ -741,11 +748,16 @@ __device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const De
       strow<CPT>(A.post + ((int64_t)tile * P.post_rows + row) * W, lane, val);
     }
   };
+  // the primary target t's row (a fused pair's targets are enumerated in
+  // F-block order, OP maps them back to the task's own rows)
+  auto out_row = [&](int64_t t) -> int64_t {
+    const DTask &Tt = P.tasks[it.task];
+    return Tt.dst_row + (fz ? (int64_t)__ldg(P.ipool + Tt.op_off + t) : t);
+  };
   auto sec_row = [&](int64_t f, int k) {
     const DTask &Tt = P.tasks[it.task];
     return Tt.sec_dst_row + __ldg(P.ipool + Tt.osf_off + f) + __ldg(P.ipool + Tt.osk_off + k);
   };
-  for (int k = 0; k < nb2; ++k) strow<CPT>(sec + (int64_t)k * W, lane, vzero<CPT>());
   // the secondary targets of F-block fb from shared memory (zeroed for the
   // next F-block); a separator ratio needs phi*, so the divisors of two
   // targets are requested together
@@ -776,7 +788,6 @@ __device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const De
       }
     }
   };
-
   // the divisor rows (phi*) of an F-block's secondary targets are requested
   // into L2 when the F-block starts, so that its flush finds them there
   auto prefetch_sec = [&](int64_t fb) {
@@ -788,39 +799,38 @@ __device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const De
       asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
     }
   };
-  prefetch_sec(it.t0 / a);
-  const int32_t t_first = (int32_t)it.t0;
-  const int32_t count = (int32_t)(it.nt * (int64_t)U);
+
+  int32_t t_first, u_first, count;
+  item_rows(it, U, t_first, u_first, count);
+  // relative row at which the next F-block ends (a fused item's batches
+  // stop there); the rows of an F-block are a * U consecutive rows
+  int32_t fb_next = fz ? (int32_t)((t_first / a + 1) * a - t_first) * U : 0x7fffffff;
+  if (fz) {
+    for (int k = 0; k < nb2; ++k) strow<CPT>(sec + (int64_t)k * W, lane, vzero<CPT>());
+    prefetch_sec(t_first / a);
+  }
   Vec<CPT> acc = vzero<CPT>(), comp = vzero<CPT>(), part = vzero<CPT>();
-  for (int32_t b0 = 0; b0 < count; b0 += 32) {
-    const int nb = min(32, count - b0);
-    const int32_t f = b0 + min(lane, nb - 1);
+  for (int32_t b0 = 0; b0 < count;) {
+    const int nb = min(min(32, count - b0), fb_next - b0);
+    // lane j: indices of row b0 + j, rows flattened as (t, u)
+    const int32_t f = u_first + b0 + min(lane, nb - 1);
     const int32_t tj = t_first + f / U, uj = f - (f / U) * U;
-    const int32_t ej = __ldg(At + tj) + __ldg(Bt + uj);
-    const int32_t xj = root ? 0 : __ldg(sAt + tj) + __ldg(sBt + uj);
-    const int32_t kj = __ldg(Ku + uj);
-    const unsigned last = __ballot_sync(kFull, uj == U - 1 && lane < nb);
-    const unsigned fend = __ballot_sync(kFull, uj == U - 1 && (tj % a) == a - 1 && lane < nb) &
-                          (it.npieces == 1 ? kFull : 0u);
-    // the batch's second group into L2 (the loop requests two groups ahead)
-    if (G < nb) {
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const float *pa = psi + (int64_t)__shfl_sync(kFull, ej, min(G + g, nb - 1)) * W + lane * CPT;
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
-      }
-    }
+    const int32_t ej = __ldg(P.ipool + (fz ? T.fA_off : T.A_off) + tj) + __ldg(P.ipool + (fz ? T.fB_off : T.B_off) + uj);
+    const int32_t xj =
+        root ? 0 : __ldg(P.ipool + (fz ? T.fsA_off : T.sA_off) + tj) + __ldg(P.ipool + (fz ? T.fsB_off : T.sB_off) + uj);
+    const int32_t kj = fz ? __ldg(P.ipool + T.ku_off + uj) : 0;
+    const unsigned last = __ballot_sync(kFull, !it.split && uj == U - 1 && lane < nb);
     for (int r = 0; r < nb; r += G) {
       Vec<CPT> p[G];
 #pragma unroll
       for (int g = 0; g < G; ++g)
         p[g] = ldrow<CPT, LD_STREAM>(psi + (int64_t)__shfl_sync(kFull, ej, min(r + g, nb - 1)) * W, lane);
-      // rows two groups ahead are requested into L2 now (the group is half
-      // the plain item's, for registers; the prefetch keeps the bytes in flight)
-      if (r + 2 * G < nb) {
+      // the next group's rows are requested into L2 now: more bytes in
+      // flight at the register-limited occupancy, without holding registers
+      if (r + G < nb) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          const float *pa = psi + (int64_t)__shfl_sync(kFull, ej, min(r + 2 * G + g, nb - 1)) * W + lane * CPT;
+          const float *pa = psi + (int64_t)__shfl_sync(kFull, ej, min(r + G + g, nb - 1)) * W + lane * CPT;
           asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
         }
       }
@@ -832,37 +842,46 @@ __device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const De
 #pragma unroll
         for (int g = 0; g < G; ++g) vmul<CPT>(p[g], q[g]);
       } else {
+        const Vec<CPT> rs = root_scale();
 #pragma unroll
         for (int g = 0; g < G; ++g) vmul<CPT>(p[g], rs);
       }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         if (r + g < nb) {
-          // the secondary target of this row, summed in shared memory
-          float *srow = sec + (int64_t)__shfl_sync(kFull, kj, r + g) * W;
-          Vec<CPT> sv = ldrow<CPT>(srow, lane);
-          vadd<CPT>(sv, p[g]);
-          strow<CPT>(srow, lane, sv);
+          if (fz) {  // the secondary target of this row, summed in shared memory
+            float *srow = sec + (int64_t)__shfl_sync(kFull, kj, r + g) * W;
+            Vec<CPT> sv = ldrow<CPT>(srow, lane);
+            vadd<CPT>(sv, p[g]);
+            strow<CPT>(srow, lane, sv);
+          }
           vadd<CPT>(part, p[g]);
           if ((last >> (r + g)) & 1u) {  // primary target complete
             kahan_fold<CPT>(acc, comp, part);
-            const int32_t t = __shfl_sync(kFull, tj, r + g);
-            const DTask &Tt = P.tasks[it.task];
-            write(Tt.kind, Tt.dst_row + __ldg(P.ipool + Tt.op_off + t), acc);
+            write(P.tasks[it.task].kind, out_row(__shfl_sync(kFull, tj, r + g)), acc);
             acc = vzero<CPT>();
             comp = vzero<CPT>();
-          }
-          if ((fend >> (r + g)) & 1u) {  // F-block complete: its secondary targets
-            const int64_t fb = __shfl_sync(kFull, tj, r + g) / a;
-            flush_sec(fb);
-            if ((fb + 1) * a < (int64_t)it.t0 + it.nt) prefetch_sec(fb + 1);
           }
         }
       }
       kahan_fold<CPT>(acc, comp, part);
     }
+    b0 += nb;
+    if (b0 == fb_next) {  // an F-block ended with this batch
+      if (it.npieces == 1) {  // a whole F-block: its secondary targets
+        const int64_t fb = (int64_t)(t_first + (b0 - 1) / U) / a;
+        flush_sec(fb);
+        if (b0 < count) prefetch_sec(fb + 1);
+      }
+      // whole F-blocks: the next one ends inside the item (no overflow)
+      if (b0 < count) fb_next += a * U;
+    }
   }
-  if (it.npieces > 1) {
+  if (it.split) {
+    Vec<CPT> tot;
+    if (combine_split<CPT>(it, P, A, tile, lane, acc, tot)) write(P.tasks[it.task].kind, out_row(it.t0), tot);
+  }
+  if (fz && it.npieces > 1) {
     // a piece of an F-block: partial secondary sums, combined in piece order
     // by the last piece to finish
     float *pbase = A.partial + ((int64_t)tile * P.n_partials + it.partial) * W;
@@ -896,13 +915,6 @@ __device__ __forceinline__ void distribute_fused_item(const DevPlan &P, const De
   }
 }
 
-// A distribute unit: a fused pair's item or a single task's item.
-template <int CPT, LoadMode RHO>
-__device__ __forceinline__ void distribute_unit(const DevPlan &P, const DevArena &A, const DItem &it, int tile,
-                                                int lane, float *sec) {
-  if (it.fused) distribute_fused_item<CPT, RHO>(P, A, it, tile, lane, sec);
-  else distribute_item<CPT, RHO>(P, A, it, tile, lane);
-}
 
 // Distribute kernel instantiations (MODE): kPlain for plans with stored
 // clique tables and no fused items, at the plain item's register budget
@@ -926,7 +938,7 @@ __device__ __forceinline__ unsigned char *dist_warp_smem(const DevPlan &P, unsig
 template <int CPT, int MODE, LoadMode RHO>
 __device__ __forceinline__ void dist_unit(const DevPlan &P, const DevArena &A, const DItem &it, int tile, int lane,
                                           unsigned char *ws) {
-  if constexpr (MODE == kFused) distribute_unit<CPT, RHO>(P, A, it, tile, lane, reinterpret_cast<float *>(ws));
+  if constexpr (MODE == kFused) distribute_pair_item<CPT, RHO>(P, A, it, tile, lane, reinterpret_cast<float *>(ws));
   else if constexpr (MODE == kRecomp) distribute_item<CPT, RHO, true>(P, A, it, tile, lane, ws);
   else distribute_item<CPT, RHO>(P, A, it, tile, lane);
 }
@@ -1048,16 +1060,21 @@ template <int CPT, int MODE>
 __global__ void __launch_bounds__(kThreads, dist_blocks_per_sm(MODE)) k_distribute_flow(DevPlan P, DevArena A) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int lane = threadIdx.x & 31;
-  unsigned char *ws = dist_warp_smem<CPT, MODE>(P, dsm, threadIdx.x >> 5);
   int64_t item;
   int tile;
   while (next_unit(A.queue + 16, P.d_flow_pref, P.d_flow_begin, P.n_flow_layers, A.tiles, lane, item, tile)) {
-    const DItem it = P.ditems[item];
+    {
+      // nothing of the scheduling is kept in registers through the item
+      const DItem &it = P.ditems[item];
+      const uint32_t c = P.tasks[it.task].clique;
+      const uint32_t need = P.d_need[c];
+      if (need == 0u ||
+          wait_ready(A.ready + ((int64_t)tile * 2 + 1) * P.n_cliques + c, need, A.errflag, P.wait_limit_ns, lane))
+        dist_unit<CPT, MODE, LD_PLAIN>(P, A, it, tile, lane, dist_warp_smem<CPT, MODE>(P, dsm, threadIdx.x >> 5));
+    }
+    const DItem &it = P.ditems[item];
     const DTask &T = P.tasks[it.task];
     uint32_t *ready = A.ready + ((int64_t)tile * 2 + 1) * P.n_cliques;
-    const uint32_t need = P.d_need[T.clique];
-    if (need == 0u || wait_ready(ready + T.clique, need, A.errflag, P.wait_limit_ns, lane))
-      dist_unit<CPT, MODE, LD_PLAIN>(P, A, it, tile, lane, ws);
     // a fused item also completes its share of the secondary child's ratio
     if (MODE == kFused && it.fused && T.sec_kind == TASK_CHILD) {
       __threadfence();
