@@ -430,19 +430,24 @@ def run_reference(args, name, net, ev, rank, world):
     o.infer(ev[:cores], threads=cores)
     t_one = max(time.perf_counter() - t0, 1e-6)
     per_step = int(min(ev.shape[0], cores * max(1, min(8, int(1.0 / t_one)))))
+    t_step = t_one
     for i in range(args.warmup):
+        t0 = time.perf_counter()
         o.infer(ev[:per_step], threads=cores)
+        t_step = time.perf_counter() - t0
+    # no --steps: as many steps as fill about ten seconds (3 to 20)
+    steps = args.steps if args.steps > 0 else max(3, min(20, int(10.0 / max(t_step, 1e-3))))
     times = []
-    for i in range(args.steps):
+    for i in range(steps):
         sl = ev[(i * per_step) % ev.shape[0]:][:per_step]
         t0 = time.perf_counter()
         o.infer(sl, threads=cores)
         times.append(time.perf_counter() - t0)
-    total = float(np.sum(times))
-    value = per_step * args.steps / total
+    total = max(float(np.sum(times)), 1e-9)
+    value = per_step * steps / total
     line = {"metric": METRIC, "value": value,
-            "unit": "cases/s", "impl": "reference", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "unit": "cases/s", "impl": "reference", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOADS[name], "cases_per_step": per_step},
             "cpu_baseline": {"value": value, "unit": "cases/s", "cores": cores, "kind": "oracle",

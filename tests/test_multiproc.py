@@ -105,3 +105,19 @@ def test_gpus_flag_spawns_ranks():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["n_gpus"] == 2 and d["impl"] == "reference" and d["metric"] == bench.METRIC
+
+
+def test_reference_arm_without_steps():
+    """`bench.py --impl reference` with no --steps picks its own step count
+    (as the GPU arm does) and prints one line."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload", "bn20"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and 3 <= d["steps"] <= 20 and d["value"] > 0
