@@ -689,6 +689,8 @@ def main():
     if rank == 0 and not args.no_cpu_layers and not observed_set:
         cpu_layers = _cpu_layers_rate(plan, ev)
 
+    # the batch's table arena is released before the serving pools are made
+    plan.close()
     serving = None
     if rank == 0 and not args.no_serving and world == 1:
         serving = {"batch_slots": run_serving(arena_gb=48.0), "rolling": run_serving(rolling=True)}
