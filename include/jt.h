@@ -228,12 +228,13 @@ typedef struct {
                                  distribute pairs are not used with it;
                                  ignored for plans specialised to an
                                  observed set.  0 (default): stored. */
-  int32_t collect_prefetch;   /* 1: the collect pass requests each child
-                                 message's rows of the next row group into
-                                 L2 while it multiplies the current group
-                                 (helps where the messages do not fit L2,
-                                 costs instructions elsewhere); 0 (default):
-                                 off.  jt_autotune tries it per plan. */
+  int32_t collect_prefetch;   /* 1: the collect pass requests the child
+                                 message rows of each 32-row batch into L2
+                                 when the batch starts, so the gathers of
+                                 its row groups find them there (helps where
+                                 the messages do not fit L2, costs
+                                 instructions elsewhere); 0 (default): off.
+                                 jt_autotune tries it per plan. */
 } jt_compile_opts;
 
 typedef struct {

@@ -389,12 +389,10 @@ __device__ __forceinline__ int load_clique_maps(const DevPlan &P, const DevArena
 // digit differs from the case's state -- the collect pass's reduction and
 // extension, in one fixed order (so a recomputed row equals the stored one
 // bit for bit).
-// prefetch: the next group's rows of every child message are requested into
-// L2 after this group's loads.
 template <int CPT, int G, LoadMode MSG, bool SLICED>
 __device__ __forceinline__ void clique_rows(const DevArena &A, const MapSmem<CPT> &sm, const float *__restrict__ base,
                                             const int32_t (&boff)[CPT], bool sliced, float bj, int32_t fj, int nchild,
-                                            int nm, int r, int nb, int lane, bool prefetch, Vec<CPT> (&v)[G]) {
+                                            int nm, int r, int nb, int lane, Vec<CPT> (&v)[G]) {
   constexpr int W = 32 * CPT;
   if (!sliced) {
 #pragma unroll
@@ -419,15 +417,6 @@ __device__ __forceinline__ void clique_rows(const DevArena &A, const MapSmem<CPT
 #pragma unroll
       for (int g = 0; g < G; ++g)
         m1[g] = ldrow<CPT, MSG>(mp1 + (int64_t)sm.idx[(i + 1) * 32 + min(r + g, nb - 1)] * W, lane);
-    }
-    if (prefetch && r + G < nb) {
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(mp0 + (int64_t)sm.idx[i * 32 + min(r + G + g, nb - 1)] * W + lane * CPT));
-        if (two)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(mp1 + (int64_t)sm.idx[(i + 1) * 32 + min(r + G + g, nb - 1)] * W +
-                                                          lane * CPT));
-      }
     }
     {
       const Vec<CPT> sc = ldrow<CPT>(sm.mval + i * W, lane);
@@ -520,9 +509,18 @@ __device__ __forceinline__ void collect_item(const DevPlan &P, const DevArena &A
     for (int i = 0; i < nm; ++i) sm.idx[i * 32 + lane] = __ldg(P.ipool + sm.mA[i] + sj) + __ldg(P.ipool + sm.mB[i] + uj);
     const unsigned last = __ballot_sync(kFull, !it.split && uj == R - 1 && lane < nb);
     __syncwarp();
+    // collect_prefetch: the batch's child-message rows are requested into L2
+    // at once (lane j: row j's), so every group's gathers find them there
+    if (P.msg_prefetch != 0 && lane < nb) {
+      for (int i = 0; i < nchild; ++i) {
+        const float *pr = A.psi + sm.mrow[i] + (int64_t)sm.idx[i * 32 + lane] * W;
+#pragma unroll
+        for (int l = 0; l < W / 32; ++l) asm volatile("prefetch.global.L2 [%0];" ::"l"(pr + 32 * l));
+      }
+    }
     for (int r = 0; r < nb; r += G) {
       Vec<CPT> v[G];
-      clique_rows<CPT, G, MSG, SLICED>(A, sm, base, boff, sliced, bj, fj, nchild, nm, r, nb, lane, P.msg_prefetch != 0, v);
+      clique_rows<CPT, G, MSG, SLICED>(A, sm, base, boff, sliced, bj, fj, nchild, nm, r, nb, lane, v);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         if (r + g < nb) {
@@ -649,7 +647,7 @@ __device__ __forceinline__ void distribute_item(const DevPlan &P, const DevArena
     for (int r = 0; r < nb; r += G) {
       Vec<CPT> p[G];
       if (recomp) {
-        clique_rows<CPT, G, LD_NC, false>(A, sm, base, no_off, false, bj, 0, nchild, nm, r, nb, lane, false, p);
+        clique_rows<CPT, G, LD_NC, false>(A, sm, base, no_off, false, bj, 0, nchild, nm, r, nb, lane, p);
       } else {
 #pragma unroll
         for (int g = 0; g < G; ++g)

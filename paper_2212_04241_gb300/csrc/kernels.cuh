@@ -50,7 +50,7 @@ struct DevPlan {
   int32_t rescale;           // 1: messages scaled by 2^-k (k per case and message)
   int32_t recompute;         // 1: no stored clique tables; the distribute pass recomputes them
   int32_t max_maps;          // most maps of a clique (the warp's shared-memory map layout)
-  int32_t msg_prefetch;      // 1: collect requests the next row group's child-message rows into L2
+  int32_t msg_prefetch;      // 1: collect requests each batch's child-message rows into L2 when it starts
   int32_t sec_rows;          // shared-memory rows (W floats) per warp of the distribute kernels (fused pairs)
   int64_t fused_items;       // fused items in the work lists (0: the plain distribute kernels)
   int64_t psi_rows;          // rows of one tile's psi region (sum |C|)
