@@ -64,6 +64,7 @@ MEASURED_TRAFFIC = {
     ("bn420", 896, (768, (0,) * 32, 1), "c144a3405c3ce8c9"): 256720000000 + 25940000000,
     ("bn420", 896, (768, (0,) * 32, 1), "7dbc36f1415f70b1"): 257730000000 + 26180000000,
     ("bn420", 896, (768, (0,) * 32, 1), "a0d3b1563434d06a"): 254860000000 + 23520000000,
+    ("bn420", 896, (768, (0,) * 32, 1), "c591329aa84cabcf"): 254850000000 + 23530000000,
 }
 
 
