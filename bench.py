@@ -310,10 +310,16 @@ SERVING_PLANS = ["bn60", "bn110", "bn420", "bn1000"]
 # in flight put more of the large plans' work in front of the small ones).
 ROLLING_TILES = {"bn60": 16, "bn1000": 16, "bn110": 8, "bn420": 6}
 SERVING_POOL_GB = 96.0
+# batch-slot serving: work items per tile and layer per plan (others: the
+# library default) and the plans whose batches run on the high-priority
+# streams (jt_server_set_priority)
+SERVING_ITEMS = {}
+SERVING_HIGH = ()
 
 
 def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, max_batch: int = 64,
-                arena_gb: float = SERVING_POOL_GB, schedule=None, min_requests: int = 20000, rolling: bool = False):
+                arena_gb: float = SERVING_POOL_GB, schedule=None, min_requests: int = 20000, rolling: bool = False,
+                items_per_tile: dict = None, high_priority=None):
     """The serving mix: resident plans of the four networks, one-case requests
     on a uniformly chosen plan with 5-30 % observed, Poisson arrivals at
     fractions of the measured saturated rate.  Returns p50/p99 latency
@@ -330,7 +336,10 @@ def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, 
     # runs layer by layer (a persistent dataflow pass would hold every SM
     # until it ends and queue the other plans' short passes behind it)
     sched = J.JT_SCHEDULE_LAYERS if schedule is None else schedule
-    plans = [J.Plan(n, cases_per_thread=1, schedule=sched) for n in nets]
+    items_per_tile = SERVING_ITEMS if items_per_tile is None else items_per_tile
+    high_priority = SERVING_HIGH if high_priority is None else high_priority
+    plans = [J.Plan(n, cases_per_thread=1, schedule=sched, items_per_tile=items_per_tile.get(nm, 0))
+             for nm, n in zip(SERVING_PLANS, nets)]
     pool = [sample_cases(n, 2048, (0.05, 0.30), seed + i) for i, n in enumerate(nets)]
 
     def drive(srv, pids, n_req, rate):
@@ -358,7 +367,11 @@ def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, 
     def fresh():
         srv = J.Server(arena_bytes=int(arena_gb * (1 << 30)), max_batch=max_batch, max_inflight=8)
         if not rolling:
-            return srv, [srv.add_plan(pl) for pl in plans]
+            pids = [srv.add_plan(pl) for pl in plans]
+            for nm, pid in zip(SERVING_PLANS, pids):
+                if nm in high_priority:
+                    srv.set_priority(pid, True)
+            return srv, pids
         pids = [None] * len(plans)
         for i, nm in enumerate(SERVING_PLANS):   # the small plans first
             if nm not in ROLLING_TILES:
@@ -388,6 +401,8 @@ def run_serving(duration_s: float = 3.0, rates=(0.25, 0.5, 0.9), seed: int = 7, 
            "mode": ("rolling tiles (iteration-level batching) for " + ", ".join(sorted(ROLLING_TILES)) +
                     (", batch slots for the others" if set(ROLLING_TILES) != set(SERVING_PLANS) else ""))
            if rolling else "batch slots",
+           "items_per_tile": dict(items_per_tile) or None,
+           "high_priority": list(high_priority) or None,
            "saturated_cases_per_s": sat, "rates": []}
     if rolling:
         out["tiles"] = dict(tiles_used)

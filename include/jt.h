@@ -538,6 +538,17 @@ JT_API jt_status jt_server_stats(jt_server *srv, int64_t *out);
  */
 JT_API jt_status jt_server_plan_stats(jt_server *srv, int32_t plan_id, int64_t *out);
 /*
+ * Scheduling class of a batch-slot plan: high != 0 runs its batches on
+ * streams of the highest priority, so when SMs free up the blocks of its
+ * passes are dispatched before those of default-priority batches (a small
+ * plan's short passes then need not wait behind a large plan's many
+ * blocks).  Default 0; applies to batches launched after the call; results
+ * do not depend on it.  Rolling plans always run at the highest priority.
+ * JT_ENOTFOUND for an unknown plan id.  Serving has no counterpart in the
+ * paper (Section 2 runs one query at a time).
+ */
+JT_API jt_status jt_server_set_priority(jt_server *srv, int32_t plan_id, int32_t high);
+/*
  * Forget the latency samples collected so far (for every plan), e.g. after
  * a warm-up; the counters and the resident slots are kept.
  */

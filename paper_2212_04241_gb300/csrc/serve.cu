@@ -17,8 +17,9 @@
 // Every device and pinned host buffer and every stream is created by
 // jt_server_create and jt_server_add_plan: the pool (one device allocation
 // of the server's arena budget, sub-allocated first-fit with coalescing),
-// max_inflight streams and events, and per plan max_inflight pairs of
-// staging buffers.  The worker itself allocates nothing.
+// 2 x max_inflight streams (default and highest priority) and events, and
+// per plan max_inflight pairs of staging buffers.  The worker itself
+// allocates nothing.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -118,6 +119,7 @@ struct PlanEntry {
   std::vector<int64_t> latencies;
   int64_t completed = 0, batches = 0;
   std::unique_ptr<Roll> roll;  // iteration-level batching (else batch slots)
+  int32_t high = 0;            // batches run on the high-priority streams
 };
 
 }  // namespace
@@ -240,8 +242,11 @@ bool slot_launch(jt_server *S, Slot &s, std::vector<Request> &&reqs) {
   jt_plan *pl = pe.plan;
   const Plan &P = pl->P;
   const int nb = (int)reqs.size();
-  int si = 0;
-  while (S->stream_busy[si]) ++si;  // admission guarantees a free stream
+  // streams [0, max_inflight) run at the default priority, the next
+  // max_inflight at the highest; fewer than max_inflight batches are in
+  // flight, so the plan's class has a free stream
+  int si = pe.high ? S->max_inflight : 0;
+  while (S->stream_busy[si]) ++si;
   int ii = 0;
   while (pe.io[ii].used) ++ii;      // and a free staging pair of the plan
   S->stream_busy[si] = 1;
@@ -596,11 +601,14 @@ extern "C" jt_status jt_server_create(int64_t arena_bytes, int32_t max_batch, in
   }
   S->pool = static_cast<char *>(pool);
   S->free_[0] = (size_t)S->budget;
-  S->streams.assign(max_inflight, nullptr);
-  S->events.assign(max_inflight, nullptr);
-  S->stream_busy.assign(max_inflight, 0);
-  for (int i = 0; i < max_inflight; ++i) {
-    if (cudaStreamCreateWithFlags(&S->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  S->streams.assign(2 * (size_t)max_inflight, nullptr);
+  S->events.assign(2 * (size_t)max_inflight, nullptr);
+  S->stream_busy.assign(2 * (size_t)max_inflight, 0);
+  for (int i = 0; i < 2 * max_inflight; ++i) {
+    if (cudaStreamCreateWithPriority(&S->streams[i], cudaStreamNonBlocking, i < max_inflight ? least : greatest) !=
+            cudaSuccess ||
         cudaEventCreateWithFlags(&S->events[i], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       server_release(S);
@@ -832,6 +840,17 @@ extern "C" jt_status jt_server_reset_latency(jt_server *S) {
   std::lock_guard<std::mutex> lk(S->mu);
   S->latencies.clear();
   for (PlanEntry &pe : S->plans) pe.latencies.clear();
+  return JT_OK;
+}
+
+extern "C" jt_status jt_server_set_priority(jt_server *S, int32_t plan_id, int32_t high) {
+  if (!S) { set_error("null argument"); return JT_EINVAL; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (plan_id < 0 || plan_id >= (int32_t)S->plans.size()) {
+    set_error("unknown plan id");
+    return JT_ENOTFOUND;
+  }
+  S->plans[plan_id].high = high ? 1 : 0;
   return JT_OK;
 }
 

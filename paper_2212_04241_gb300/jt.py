@@ -72,7 +72,8 @@ EXPORTS = ["jt_default_opts", "jt_compile", "jt_autotune", "jt_infer", "jt_infer
            "jt_profile", "jt_debug_stall",
            "jt_plan_info", "jt_plan_clique", "jt_plan_free", "jt_status_string", "jt_last_error",
            "jt_server_create", "jt_server_add_plan", "jt_server_add_plan_rolling", "jt_submit", "jt_poll", "jt_server_drain",
-           "jt_server_stats", "jt_server_plan_stats", "jt_server_reset_latency", "jt_server_destroy"]
+           "jt_server_stats", "jt_server_plan_stats", "jt_server_set_priority", "jt_server_reset_latency",
+           "jt_server_destroy"]
 
 
 def _load():
@@ -105,6 +106,7 @@ def _load():
         "jt_server_stats": ([P, P], ctypes.c_int),
         "jt_server_plan_stats": ([P, I32, P], ctypes.c_int),
         "jt_server_reset_latency": ([P], ctypes.c_int),
+        "jt_server_set_priority": ([P, I32, I32], ctypes.c_int),
         "jt_server_destroy": ([P], None),
     }
     for name in EXPORTS:
@@ -353,6 +355,10 @@ class Server:
 
     def reset_latency(self):
         _check(lib.jt_server_reset_latency(self._h))
+
+    def set_priority(self, plan_id: int, high: bool = True):
+        """Run the plan's batches on the high-priority streams (jt_server_set_priority)."""
+        _check(lib.jt_server_set_priority(self._h, int(plan_id), 1 if high else 0))
 
     def plan_stats(self, plan_id: int) -> dict:
         out = np.zeros(4, dtype=np.int64)

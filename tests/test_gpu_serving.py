@@ -283,3 +283,35 @@ def test_rolling_refuses_tiles_beyond_the_pool(plans):
         srv.add_plan(plan, rolling_tiles=1 << 16)
     assert e.value.status == J.JT_ENOMEM
     srv.close()
+
+
+def test_priority_class_changes_no_result(plans):
+    """jt_server_set_priority moves a plan's batches to the high-priority
+    streams; the same requests give the same results bit for bit with and
+    without it, and an unknown plan id is refused."""
+    srv = J.Server(arena_bytes=8 << 30, max_batch=32, max_inflight=4)
+    pids = [srv.add_plan(p) for _, _, p in plans]
+    reqs = []
+    for pi, (nm, net, plan) in enumerate(plans):
+        for e in configs.evidence(nm, net, n_cases=24, seed=700 + pi):
+            reqs.append((pi, e))
+
+    def run():
+        tickets, out_len = [], {}
+        for pi, e in reqs:
+            t = srv.submit(pids[pi], e)
+            tickets.append(t)
+            out_len[t] = plans[pi][2].sum_card
+        res = _wait(srv, tickets, out_len)
+        return [res[t] for t in tickets]
+
+    before = run()
+    for pid in pids[::2]:
+        srv.set_priority(pid, True)
+    after = run()
+    for a, b in zip(before, after):
+        assert a[0] == b[0] and a[2] == b[2] and np.array_equal(a[1], b[1])
+    with pytest.raises(J.JTError) as e:
+        srv.set_priority(len(pids) + 3, True)
+    assert e.value.status == J.JT_ENOTFOUND
+    srv.close()
