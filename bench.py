@@ -65,6 +65,7 @@ MEASURED_TRAFFIC = {
     ("bn420", 896, (768, (0,) * 32, 1), "7dbc36f1415f70b1"): 257730000000 + 26180000000,
     ("bn420", 896, (768, (0,) * 32, 1), "a0d3b1563434d06a"): 254860000000 + 23520000000,
     ("bn420", 896, (768, (0,) * 32, 1), "c591329aa84cabcf"): 254850000000 + 23530000000,
+    ("bn420", 896, (768, (0,) * 32, 0), "c591329aa84cabcf"): 329970000000 + 24160000000,
 }
 
 
